@@ -1,0 +1,183 @@
+"""NumPy oracle for exact RR-preselected thresholds and (averaged) determinism.
+
+TEST INFRASTRUCTURE: only the tests, the smoke check and the benchmark's CPU
+baseline use this module.
+
+Notation (Sect. 2, Eq. 1-4): a scalar series y[0..N-1] (FP32) is delay
+embedded with dimension m and delay tau (Sect. 3.3),
+    x_i = (y[i], y[i+tau], ..., y[i+(m-1)tau]),   i = 0 .. Ne-1,
+    Ne = N - (m-1) tau.
+(The paper writes the delays backwards, x(t) = [y(t), y(t-tau), ...]; indexing
+forwards gives the same set of vectors, shifted by (m-1)tau, hence the same
+distances and diagonal lines.)  Distances use the maximum norm (Sect. 2):
+    d_ij = max_q |y[i+q tau] - y[j+q tau]|        (FP32 subtract, abs, max).
+
+Readings of the paper (the paper is silent or ambiguous on these):
+
+* Only the upper triangle i < j is used (Sect. 4 computes on j > i); the line
+  of identity is excluded from every count.  P = Ne (Ne - 1) / 2 pairs.
+* RR targets are rationals rr_num / rr_den (the paper's RR in per cent is
+  rr_num / 100).  The target count is T = ceil(rr_num * P / rr_den) in exact
+  integers.
+* The threshold for a target is the T-th smallest distance, eps (Sect. 2:
+  "preselect RR and use the corresponding value for eps").  A cell is
+  recurrent iff d_ij <= eps.  (Eq. 2 sets H(0) = 0, i.e. strict d < eps; the
+  inclusive form is Eq. 1 evaluated at the next float above eps, and is the
+  only reading under which an all-equal-distance series has any recurrence.)
+  The achieved count C = #{d <= eps} satisfies #{d < eps} < T <= C.
+* DET (Eq. 4) over the upper triangle: sum_{l >= lmin} l P(l) / C, where P(l)
+  counts maximal runs of recurrent cells along each diagonal j - i = delta.
+  Both triangles hold the same lines, so the ratio equals the full-matrix ratio
+  without the line of identity.  DET is a ratio of exact integers in FP64.
+* Averaged DET (Eq. avgDET): the FP64 sum of DET over the K targets in their
+  given order, divided by K.
+"""
+from __future__ import annotations
+
+from typing import Dict, Sequence, Tuple
+
+import numpy as np
+
+
+def embedded_count(n: int, m: int, tau: int) -> int:
+    """Ne = N - (m-1) tau, the number of delay vectors (Sect. 3.3)."""
+    return int(n) - (int(m) - 1) * int(tau)
+
+
+def pair_count(ne: int) -> int:
+    """P = Ne (Ne - 1) / 2 off-diagonal pairs of the upper triangle (Sect. 4)."""
+    return ne * (ne - 1) // 2
+
+
+def target_counts(p: int, rr_num: Sequence[int], rr_den: int) -> np.ndarray:
+    """T_k = ceil(rr_num_k * P / rr_den) in exact integers (Eq. 3 inverted)."""
+    out = []
+    for r in rr_num:
+        num = int(r) * int(p)
+        out.append(-((-num) // int(rr_den)))
+    return np.array(out, dtype=np.uint64)
+
+
+def diagonal_distances(y: np.ndarray, m: int, tau: int, delta: int) -> np.ndarray:
+    """d(i, i+delta) for i = 0 .. Ne-delta-1, maximum norm in FP32 (Eq. 1)."""
+    y = np.asarray(y, dtype=np.float32)
+    ne = embedded_count(len(y), m, tau)
+    i = np.arange(ne - delta)
+    d = np.abs(y[i] - y[i + delta])
+    for q in range(1, m):
+        d = np.maximum(d, np.abs(y[i + q * tau] - y[i + delta + q * tau]))
+    return d.astype(np.float32)
+
+
+def all_distances(y: np.ndarray, m: int, tau: int) -> np.ndarray:
+    """All P upper-triangle distances, diagonal by diagonal (delta = 1 .. Ne-1)."""
+    ne = embedded_count(len(y), m, tau)
+    if ne < 2:
+        return np.zeros(0, dtype=np.float32)
+    return np.concatenate([diagonal_distances(y, m, tau, dl) for dl in range(1, ne)])
+
+
+def eps_for_rr(y: np.ndarray, m: int, tau: int, rr_num: Sequence[int], rr_den: int,
+               dist: np.ndarray = None) -> Dict[str, np.ndarray]:
+    """Exact thresholds by sorting all distances (Sect. 2, "preselect RR").
+
+    Returns eps (FP32), T, count_le = #{d <= eps}, count_lt = #{d < eps}.
+    """
+    d = all_distances(y, m, tau) if dist is None else dist
+    p = d.shape[0]
+    if p == 0:
+        raise ValueError("fewer than two embedded vectors")
+    t = target_counts(p, rr_num, rr_den)
+    s = np.sort(d, kind="stable")
+    eps = s[(t - 1).astype(np.int64)].astype(np.float32)
+    le = np.searchsorted(s, eps, side="right").astype(np.uint64)
+    lt = np.searchsorted(s, eps, side="left").astype(np.uint64)
+    return {"eps": eps, "T": t, "count_le": le, "count_lt": lt}
+
+
+def _runs(mask: np.ndarray) -> np.ndarray:
+    """Lengths of the maximal runs of True in a 1-D boolean array."""
+    if mask.size == 0:
+        return np.zeros(0, dtype=np.int64)
+    padded = np.concatenate(([False], mask, [False])).astype(np.int8)
+    diff = np.diff(padded)
+    starts = np.flatnonzero(diff == 1)
+    ends = np.flatnonzero(diff == -1)
+    return (ends - starts).astype(np.int64)
+
+
+def line_hist(y: np.ndarray, m: int, tau: int, eps: Sequence[float]) -> Dict[str, np.ndarray]:
+    """Diagonal line statistics of the upper triangle for each threshold.
+
+    For every threshold k: hist[k, l-1] = P_k(l), the number of maximal
+    diagonal runs of length l (l = 1 .. Ne-1; Eq. 4 and Sect. 4); count =
+    number of recurrent cells; stencil = recurrent cells with a recurrent
+    diagonal neighbour (i-1, j-1) or (i+1, j+1); lmax = longest run.
+    """
+    y = np.asarray(y, dtype=np.float32)
+    eps = np.asarray(eps, dtype=np.float32)
+    k = eps.shape[0]
+    ne = embedded_count(len(y), m, tau)
+    hist = np.zeros((k, max(ne - 1, 0)), dtype=np.uint64)
+    count = np.zeros(k, dtype=np.uint64)
+    stencil = np.zeros(k, dtype=np.uint64)
+    lmax = np.zeros(k, dtype=np.uint32)
+    for dl in range(1, ne):
+        d = diagonal_distances(y, m, tau, dl)
+        # rec[k, i] = R^k_{i, i+dl}: one row per threshold along this diagonal.
+        rec = d[None, :] <= eps[:, None]
+        count += rec.sum(axis=1).astype(np.uint64)
+        nb = np.zeros_like(rec)
+        nb[:, 1:] |= rec[:, :-1]
+        nb[:, :-1] |= rec[:, 1:]
+        stencil += (rec & nb).sum(axis=1).astype(np.uint64)
+        # Maximal runs: +1 where a run starts, -1 one past where it ends.
+        padded = np.zeros((k, rec.shape[1] + 2), dtype=np.int8)
+        padded[:, 1:-1] = rec
+        edge = np.diff(padded, axis=1)
+        ks, starts = np.nonzero(edge == 1)      # row-major: sorted by (k, position)
+        ke, ends = np.nonzero(edge == -1)
+        assert np.array_equal(ks, ke)
+        lens = ends - starts
+        if lens.size:
+            np.add.at(hist, (ks, lens - 1), np.uint64(1))
+            np.maximum.at(lmax, ks, lens.astype(np.uint32))
+    return {"hist": hist, "count": count, "stencil": stencil, "lmax": lmax}
+
+
+def det_from_hist(hist: np.ndarray, count: np.ndarray, lmin: Sequence[int]) -> np.ndarray:
+    """DET_k(lmin) = sum_{l >= lmin} l P_k(l) / C_k in FP64 (Eq. 4).
+
+    Returns an array of shape (K, len(lmin)).
+    """
+    k, lmax_len = hist.shape
+    out = np.zeros((k, len(lmin)), dtype=np.float64)
+    lengths = np.arange(1, lmax_len + 1, dtype=object)
+    for kk in range(k):
+        row = [int(v) for v in hist[kk]]
+        for j, lm in enumerate(lmin):
+            num = sum(int(l) * c for l, c in zip(lengths, row) if l >= lm)
+            out[kk, j] = float(num) / float(int(count[kk]))
+    return out
+
+
+def det_avg(det: np.ndarray) -> np.ndarray:
+    """Averaged DET (Eq. avgDET): FP64 sum over k in order, then / K."""
+    k = det.shape[0]
+    acc = np.zeros(det.shape[1], dtype=np.float64)
+    for kk in range(k):
+        acc = acc + det[kk]
+    return acc / np.float64(k)
+
+
+def rqa_det_avg(y: np.ndarray, m: int, tau: int, rr_num: Sequence[int], rr_den: int,
+                lmin: Sequence[int] = (2,)) -> Dict[str, np.ndarray]:
+    """The whole hot path on one series: eps_k, line statistics, DET_k, mean."""
+    sel = eps_for_rr(y, m, tau, rr_num, rr_den)
+    lines = line_hist(y, m, tau, sel["eps"])
+    det = det_from_hist(lines["hist"], lines["count"], lmin)
+    out = dict(sel)
+    out.update(lines)
+    out["det"] = det
+    out["det_avg"] = det_avg(det)
+    return out

@@ -1,0 +1,276 @@
+"""Pins of the CPU oracle to facts fixed by the paper's definitions and by
+mathematics -- not to the oracle itself.
+
+Each pin is chosen so that a plausible slip in the oracle (an off-by-one in
+the target count, a strict/inclusive mix-up, a dropped delay coordinate, a
+transposed diagonal, a lost line at a diagonal's end) fails at least one test:
+
+* a hand-worked 4-point example (tests/golden/hand_example_4pt.json);
+* brute force over the FULL N x N matrix with ordered pairs (a different
+  formulation of Eq. 1-4: every count is exactly twice the upper-triangle one);
+* closed forms: constant series, integer ramp, sawtooth;
+* invariants: selection certificate, monotonicity, histogram mass, stencil vs
+  histogram, negation / time reversal / power-of-two scaling;
+* the i.i.d.-noise expectation DET ~ 1 - (1 - r)^2 (m = 1, large N).
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import rqa_oracle as O
+from oracle import c_oracle as CO
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+RR = list(range(1, 21))
+
+
+# ---------------------------------------------------------------- hand example
+def test_hand_example_matches_worked_values():
+    g = json.load(open(os.path.join(GOLDEN, "hand_example_4pt.json")))
+    y = np.array(g["y"], dtype=np.float32)
+    r = O.rqa_det_avg(y, g["m"], g["tau"], g["rr_num"], g["rr_den"], lmin=(2,))
+    assert r["eps"].tolist() == g["eps"]
+    assert r["T"].tolist() == g["T"]
+    assert r["count_le"].tolist() == g["count_le"]
+    assert r["count_lt"].tolist() == g["count_lt"]
+    assert r["hist"].tolist() == g["hist"]
+    assert r["stencil"].tolist() == g["stencil"]
+    assert r["lmax"].tolist() == g["lmax"]
+    assert r["det"][:, 0].tolist() == g["det_lmin2"]
+    assert float(r["det_avg"][0]) == g["det_avg_lmin2"]
+
+
+# ------------------------------------------------------------ target counts
+@pytest.mark.parametrize("p", [1, 2, 3, 4753, 49975003, 4999350021, 2**62 // 100])
+def test_target_count_is_smallest_integer_reaching_rate(p):
+    for num, den in [(1, 100), (7, 100), (20, 100), (99, 100), (1, 3), (2, 7)]:
+        t = int(O.target_counts(p, [num], den)[0])
+        # T/P >= num/den and (T-1)/P < num/den, in exact rationals
+        assert Fraction(t, p) >= Fraction(num, den)
+        assert Fraction(t - 1, p) < Fraction(num, den)
+
+
+# ------------------------------------------------- full-matrix brute force
+def _d32(y, i, j, m, tau):
+    d = np.float32(0.0)
+    for q in range(m):
+        v = np.float32(abs(np.float32(y[i + q * tau]) - np.float32(y[j + q * tau])))
+        d = v if q == 0 else (v if v > d else d)
+    return d
+
+
+def _brute_full(y, m, tau, rr_num, rr_den, lmin):
+    """Full ordered-pair matrix without the line of identity, pure Python."""
+    n = len(y)
+    ne = n - (m - 1) * tau
+    D = [[_d32(y, i, j, m, tau) if i != j else None for j in range(ne)] for i in range(ne)]
+    vals = sorted({D[i][j] for i in range(ne) for j in range(ne) if i != j})
+    npairs = ne * (ne - 1)  # ordered
+    out = []
+    for num in rr_num:
+        need = -((-num * npairs) // rr_den)  # ceil over ordered pairs
+        eps = None
+        for v in vals:  # smallest distance value whose ordered count reaches the target
+            if sum(1 for i in range(ne) for j in range(ne) if i != j and D[i][j] <= v) >= need:
+                eps = v
+                break
+        rec = [[(i != j) and D[i][j] <= eps for j in range(ne)] for i in range(ne)]
+        c2 = sum(rec[i][j] for i in range(ne) for j in range(ne))
+        lt2 = sum(1 for i in range(ne) for j in range(ne) if i != j and D[i][j] < eps)
+        # lines on every diagonal of the full matrix except the main one
+        hist2 = [0] * ne
+        for off in range(-(ne - 1), ne):
+            if off == 0:
+                continue
+            run = 0
+            cells = [(i, i + off) for i in range(ne) if 0 <= i + off < ne]
+            for cell in cells + [None]:
+                if cell is not None and rec[cell[0]][cell[1]]:
+                    run += 1
+                else:
+                    if run:
+                        hist2[run] += 1
+                    run = 0
+        det = [sum(l * hist2[l] for l in range(lm, ne)) / c2 for lm in lmin]
+        out.append(dict(eps=eps, c2=c2, lt2=lt2, hist2=hist2, det=det))
+    return out
+
+
+@pytest.mark.parametrize("seed,n,m,tau", [(0, 12, 1, 1), (1, 17, 2, 1), (2, 20, 3, 2),
+                                          (3, 9, 1, 1), (4, 33, 3, 3), (5, 25, 2, 4)])
+def test_oracle_equals_full_matrix_brute_force(seed, n, m, tau):
+    rng = np.random.default_rng(seed)
+    # coarse values force many exact ties
+    y = (rng.integers(0, 6, size=n) * 0.25).astype(np.float32) if seed % 2 else \
+        rng.standard_normal(n).astype(np.float32)
+    rr_num, rr_den, lmin = [1, 5, 13, 20, 37, 50], 100, (2, 3, 5)
+    orc = O.rqa_det_avg(y, m, tau, rr_num, rr_den, lmin)
+    ref = _brute_full(y, m, tau, rr_num, rr_den, lmin)
+    for k, b in enumerate(ref):
+        assert orc["eps"][k] == b["eps"]
+        assert 2 * int(orc["count_le"][k]) == b["c2"]
+        assert 2 * int(orc["count_lt"][k]) == b["lt2"]
+        ne = n - (m - 1) * tau
+        for l in range(1, ne):
+            assert 2 * int(orc["hist"][k, l - 1]) == b["hist2"][l]
+        for j in range(len(lmin)):
+            assert orc["det"][k, j] == pytest.approx(b["det"][j], abs=0, rel=1e-15)
+
+
+# ------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("n,m,tau", [(40, 1, 1), (31, 3, 2), (64, 2, 5)])
+def test_constant_series_closed_form(n, m, tau):
+    y = np.full(n, 0.7, dtype=np.float32)
+    ne = n - (m - 1) * tau
+    p = ne * (ne - 1) // 2
+    r = O.rqa_det_avg(y, m, tau, RR, 100, lmin=(2, 3, 5))
+    assert np.all(r["eps"] == 0.0)
+    assert np.all(r["count_le"] == p) and np.all(r["count_lt"] == 0)
+    assert np.all(r["hist"] == 1)           # one line of every length 1..Ne-1
+    assert np.all(r["lmax"] == ne - 1)
+    for j, lm in enumerate((2, 3, 5)):
+        exact = 1.0 - (lm * (lm - 1) // 2) / p
+        assert np.all(r["det"][:, j] == (p - lm * (lm - 1) // 2) / p)
+        assert abs(r["det"][0, j] - exact) < 1e-15
+
+
+@pytest.mark.parametrize("n,m,tau", [(50, 1, 1), (45, 3, 2)])
+def test_ramp_closed_form(n, m, tau):
+    y = np.arange(n, dtype=np.float32)       # d_ij = j - i exactly for any m, tau
+    ne = n - (m - 1) * tau
+    p = ne * (ne - 1) // 2
+    r = O.rqa_det_avg(y, m, tau, RR, 100, lmin=(2,))
+    for k, num in enumerate(RR):
+        t = -((-num * p) // 100)
+        e = 1
+        while sum(ne - dl for dl in range(1, e + 1)) < t:
+            e += 1
+        assert r["eps"][k] == np.float32(e)
+        assert int(r["count_le"][k]) == sum(ne - dl for dl in range(1, e + 1))
+        assert int(r["count_lt"][k]) == sum(ne - dl for dl in range(1, e))
+        expect = np.zeros(ne - 1, dtype=np.uint64)
+        for dl in range(1, e + 1):
+            expect[ne - dl - 1] += 1               # diagonal dl is one full line
+        assert np.array_equal(r["hist"][k], expect)
+        assert int(r["lmax"][k]) == ne - 1
+
+
+def test_sawtooth_zero_threshold_lines():
+    p_, n = 7, 70
+    y = (np.arange(n) % p_).astype(np.float32)
+    ne = n
+    pairs = ne * (ne - 1) // 2
+    zero_cells = sum(ne - q * p_ for q in range(1, (ne - 1) // p_ + 1))
+    r = O.rqa_det_avg(y, 1, 1, RR, 100, lmin=(2,))
+    for k, num in enumerate(RR):
+        t = -((-num * pairs) // 100)
+        if t <= zero_cells:
+            assert r["eps"][k] == 0.0
+            assert int(r["count_le"][k]) == zero_cells
+            expect = np.zeros(ne - 1, dtype=np.uint64)
+            for q in range(1, (ne - 1) // p_ + 1):
+                expect[ne - q * p_ - 1] += 1
+            assert np.array_equal(r["hist"][k], expect)
+        else:
+            assert r["eps"][k] >= 1.0
+
+
+# --------------------------------------------------------------- invariants
+def _series(kind, n, seed):
+    rng = np.random.default_rng(seed)
+    if kind == "noise":
+        return rng.standard_normal(n).astype(np.float32)
+    t = np.arange(n)
+    return (np.sin(2 * np.pi * t / 20.3) + 0.1 * rng.standard_normal(n)).astype(np.float32)
+
+
+@pytest.mark.parametrize("kind,n,m,tau", [("noise", 300, 1, 1), ("sine", 400, 3, 3), ("sine", 257, 2, 1)])
+def test_invariants(kind, n, m, tau):
+    y = _series(kind, n, 11)
+    r = O.rqa_det_avg(y, m, tau, RR, 100, lmin=(2, 3, 5))
+    t = r["T"].astype(np.int64)
+    le = r["count_le"].astype(np.int64)
+    lt = r["count_lt"].astype(np.int64)
+    assert np.all(lt < t) and np.all(t <= le)                      # certificate
+    assert np.all(np.diff(r["eps"]) >= 0) and np.all(np.diff(le) >= 0)  # monotone in k
+    L = np.arange(1, r["hist"].shape[1] + 1, dtype=np.int64)
+    mass = (r["hist"].astype(np.int64) * L[None, :]).sum(axis=1)
+    assert np.array_equal(mass, le)                               # sum l P(l) = C
+    assert np.array_equal(r["count"].astype(np.int64), le)
+    s_from_hist = le - r["hist"][:, 0].astype(np.int64)
+    assert np.array_equal(r["stencil"].astype(np.int64), s_from_hist)  # S = C - P(1)
+    assert np.array_equal(r["det"][:, 0], r["stencil"].astype(np.float64) / le.astype(np.float64))
+    # independent certificate from the C oracle
+    cle, clt = CO.count(y, m, tau, r["eps"])
+    assert np.array_equal(cle.astype(np.int64), le) and np.array_equal(clt.astype(np.int64), lt)
+
+
+@pytest.mark.parametrize("m,tau", [(1, 1), (3, 2)])
+def test_metamorphic_negation_reversal_scaling(m, tau):
+    y = _series("noise", 180, 5)
+    base = O.rqa_det_avg(y, m, tau, RR, 100, lmin=(2, 3))
+    for y2, scale in [(-y, 1.0), (y[::-1].copy(), 1.0), (y * np.float32(8.0), 8.0),
+                      (y * np.float32(0.125), 0.125)]:
+        r = O.rqa_det_avg(y2, m, tau, RR, 100, lmin=(2, 3))
+        assert np.array_equal(r["eps"], (base["eps"] * np.float32(scale)).astype(np.float32))
+        for key in ("count_le", "count_lt", "hist", "stencil", "lmax", "det", "det_avg"):
+            assert np.array_equal(r[key], base[key]), key
+
+
+def test_delay_coordinates_all_used():
+    # A series whose second delay coordinate alone separates two vectors: dropping
+    # any coordinate of the maximum norm changes the distances.
+    y = np.array([0, 0, 5, 0, 0, 0, 9, 0], dtype=np.float32)
+    d = O.all_distances(y, 3, 2)
+    # vectors: x0=(0,5,0) x1=(0,0,0) x2=(5,0,9) x3=(0,0,0)
+    assert d.tolist() == [5.0, 9.0, 9.0, 9.0, 0.0, 5.0]
+
+
+# ---------------------------------------------------- statistical closed form
+def test_iid_noise_det_matches_independence_expectation():
+    """m = 1, i.i.d. Gaussian noise: off the first diagonal, neighbouring cells of
+    a diagonal use disjoint samples, so P(recurrent neighbour | recurrent) is
+    1 - (1 - r)^2 in the interior and r at a diagonal's two ends."""
+    n = 1500
+    y = np.random.default_rng(123).standard_normal(n).astype(np.float32)
+    rr = [5, 10, 20]
+    r = O.eps_for_rr(y, 1, 1, rr, 100)
+    for k, eps in enumerate(r["eps"]):
+        rate = float(r["count_le"][k]) / (n * (n - 1) / 2)
+        exp_s = 0.0
+        exp_c = 0.0
+        for dl in range(2, n):
+            ln = n - dl
+            exp_c += ln * rate
+            if ln == 1:
+                continue
+            exp_s += rate * ((ln - 2) * (1 - (1 - rate) ** 2) + 2 * rate)
+        obs = CO.lines(y, 1, 1, [eps], full_hist=False)
+        d1 = O.diagonal_distances(y, 1, 1, 1) <= eps
+        nb1 = np.zeros_like(d1)
+        nb1[1:] |= d1[:-1]
+        nb1[:-1] |= d1[1:]
+        s1 = int((d1 & nb1).sum())
+        c_off = int(obs["count"][0]) - int(d1.sum())
+        s_off = int(obs["stencil"][0]) - s1
+        det_off = s_off / c_off
+        expect = exp_s / exp_c
+        assert abs(det_off - expect) < 0.01, (rate, det_off, expect)
+        # a one-sided neighbour rule would give ~ r, far outside the band
+        assert abs(det_off - rate) > 0.03
+
+
+# --------------------------------------------- C oracle against NumPy oracle
+@pytest.mark.parametrize("n,m,tau", [(200, 1, 1), (333, 3, 3), (150, 2, 7)])
+def test_c_oracle_agrees_with_numpy_oracle(n, m, tau):
+    y = _series("sine", n, 3)
+    r = O.rqa_det_avg(y, m, tau, RR, 100)
+    assert np.array_equal(CO.distances(y, m, tau), O.all_distances(y, m, tau))
+    L = CO.lines(y, m, tau, r["eps"], full_hist=True, n_short=8)
+    for key in ("hist", "count", "stencil", "lmax"):
+        assert np.array_equal(L[key], r[key]), key
+    assert np.array_equal(L["short_hist"], r["hist"][:, :8])
