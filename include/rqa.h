@@ -1,0 +1,209 @@
+/*
+ * rqa.h -- C ABI of the GB300 (sm_103a) library for averaged recurrence
+ * quantification analysis: exact recurrence-rate-preselected thresholds and
+ * determinism, computed over never-materialised recurrence matrices.
+ *
+ * Definitions (Pánis, Adámek & Marwan, "Averaged recurrence quantification
+ * analysis"):
+ *   series       y[0..N-1], FP32, delay embedded with dimension m and delay
+ *                tau (Sect. 3.3): x_i = (y[i], y[i+tau], ..., y[i+(m-1)tau]),
+ *                i < Ne = N - (m-1) tau.
+ *   distance     d_ij = max_q |y[i+q tau] - y[j+q tau]|, maximum norm (Sect. 2).
+ *   recurrence   R_ij = [d_ij <= eps] (Eq. 1-2; see below for the boundary).
+ *   upper        only pairs i < j are used (Sect. 4); P = Ne(Ne-1)/2 pairs.
+ *   RR target    rr_num/rr_den of the P pairs (Eq. 3, "preselect RR").
+ *   eps_k        the T_k-th smallest distance, T_k = ceil(rr_num_k * P / rr_den).
+ *                Cells with d <= eps_k are recurrent, so #{d < eps_k} < T_k
+ *                <= #{d <= eps_k}.  (Eq. 2 has H(0) = 0; the inclusive test is
+ *                Eq. 1 taken at the next float above eps_k.)
+ *   lines        maximal runs of recurrent cells along a diagonal j - i = const;
+ *                P_k(l) = number of such runs of length l (Eq. 4).
+ *   DET_k(lmin)  sum_{l >= lmin} l P_k(l) / #{d <= eps_k}   (Eq. 4), FP64 ratio
+ *                of exact integer counts.
+ *   DET average  (1/K) sum_k DET_k, summed in k order   (Eq. avgDET, Sect. 2).
+ *
+ * Conventions for every entry point:
+ *   - Pointers documented "device" must be device memory of cfg.device;
+ *     "host" pointers are read before the call returns.  The caller owns every
+ *     input and output buffer; the context owns its scratch memory.
+ *   - Work is enqueued on the context's stream (cfg.stream) and is
+ *     asynchronous: outputs are valid after the stream is synchronised.
+ *     Errors found on the host return at once; errors found by the kernels
+ *     (non-finite input, unsorted thresholds, capacity, time-outs) are
+ *     reported by rqa_status().
+ *   - A context is not thread safe; use one per host thread.
+ *   - K (number of thresholds per series) is 1 .. RQA_K_MAX.
+ *   - A series must have Ne >= 2 (P >= 1), otherwise RQA_ERR_TOO_SHORT.
+ */
+#ifndef RQA_H
+#define RQA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RQA_ABI_VERSION 1
+#define RQA_K_MAX 31          /* thresholds per series and call */
+#define RQA_M_MAX 16          /* embedding dimension */
+#define RQA_LMIN_MAX 8        /* entries of the lmin list of rqa_det_avg */
+#define RQA_SKETCH_PAIRS 4096 /* random pairs of the distance sketch */
+#define RQA_SKETCH_BINS 128   /* quantiles kept from the sketch */
+#define RQA_FEATURES 131      /* sketch bins + log10 N, m, tau */
+
+/* Return codes. */
+enum {
+    RQA_OK = 0,
+    RQA_ERR_INVALID_ARG = 1, /* NULL pointer, K or m or tau out of range, bad rr */
+    RQA_ERR_TOO_SHORT = 2,   /* a series has fewer than two embedded vectors */
+    RQA_ERR_NONFINITE = 3,   /* device: a series holds NaN or +-Inf */
+    RQA_ERR_CUDA = 4,        /* a CUDA runtime call failed (no device, launch) */
+    RQA_ERR_OOM = 5,         /* scratch allocation failed */
+    RQA_ERR_TIMEOUT = 6,     /* device: a bounded wait gave up */
+    RQA_ERR_CAPACITY = 7,    /* output buffer too small / size limit exceeded */
+    RQA_ERR_UNSORTED = 8,    /* device: thresholds of a series not ascending */
+    RQA_ERR_NO_MODEL = 9,    /* bracket selection requested without a model */
+    RQA_ERR_INTERNAL = 10    /* device: inconsistent counts (a library bug) */
+};
+
+/* Work schedule: one persistent launch per phase over the whole batch, or one
+ * launch sequence per series (the plain per-series form). */
+enum { RQA_SCHED_BATCHED = 0, RQA_SCHED_PER_SERIES = 1 };
+
+/* Threshold selection: full radix select over FP32 bit patterns (3 counting
+ * passes), or the learned bracket (2 passes when the bracket holds, radix
+ * fallback per threshold when it misses).  AUTO = bracket if a model is set. */
+enum { RQA_SELECT_AUTO = 0, RQA_SELECT_RADIX = 1, RQA_SELECT_BRACKET = 2 };
+
+typedef struct rqa_ctx rqa_ctx;
+
+typedef struct {
+    int device;        /* CUDA device ordinal */
+    void *stream;      /* cudaStream_t owned by the caller; NULL = default stream */
+    int schedule;      /* RQA_SCHED_* */
+    int select;        /* RQA_SELECT_* */
+    int band;          /* diagonals per warp band: 0 = tuned default, else 8/16/32 */
+    int blocks_per_sm; /* persistent CTAs per SM: 0 = tuned default */
+    int reserved[4];   /* must be zero */
+} rqa_config;
+
+/* A batch of S series stored back to back in one device buffer. */
+typedef struct {
+    const float *y;          /* device, offsets[S] FP32 values, caller-owned */
+    const int64_t *offsets;  /* host, S+1 ascending, offsets[0] = 0 */
+    const int32_t *m;        /* host, S embedding dimensions, 1..RQA_M_MAX */
+    const int32_t *tau;      /* host, S delays, >= 1 */
+    int32_t n_series;        /* S >= 1 */
+} rqa_batch;
+
+/* ---- lifetime ------------------------------------------------------------ */
+
+/* Create a context on cfg->device.  cfg may be NULL (device 0, default
+ * stream, batched, auto select).  Returns RQA_ERR_CUDA if the device cannot be
+ * used.  *out is NULL on failure. */
+int rqa_create(rqa_ctx **out, const rqa_config *cfg);
+
+/* Release the context and its scratch (synchronises its stream first). */
+void rqa_destroy(rqa_ctx *ctx);
+
+/* Synchronise the context's stream and return the first error any kernel
+ * recorded since the last call (then clear it), or a pending CUDA error. */
+int rqa_status(rqa_ctx *ctx);
+
+/* Static description of a return code. */
+const char *rqa_error_string(int code);
+
+int rqa_abi_version(void);
+
+/* Number of SMs of the context's device and the schedule parameters in use
+ * (band, blocks per SM); any pointer may be NULL. */
+int rqa_device_info(rqa_ctx *ctx, int *sm_count, int *band, int *blocks_per_sm);
+
+/* Per-phase device times of the context's last hot-path call, in ms, when
+ * timing is on (rqa_set_timing): [0] finiteness check, [1] coarse counting
+ * round + selection, [2] middle round, [3] final round, [4] line pass,
+ * [5] finalisation.  Synchronises the stream.  n >= 6.  Batched schedule
+ * only (per-series calls report zeros). */
+int rqa_set_timing(rqa_ctx *ctx, int enable);
+int rqa_phase_times(rqa_ctx *ctx, float *ms, int n);
+
+/* Number of kernels this context has launched since it was created. */
+uint64_t rqa_kernel_launches(rqa_ctx *ctx);
+
+/* ---- host helpers (no GPU needed) -------------------------------------- */
+
+/* T_k = ceil(rr_num[k] * P / rr_den) in exact integer arithmetic (Eq. 3
+ * inverted).  rr_num[k] in 1..rr_den-1, P >= 1.  Host pointers. */
+int rqa_target_counts(uint64_t P, const int32_t *rr_num, int32_t rr_den, int32_t K,
+                      uint64_t *T_out);
+
+/* ---- the hot path -------------------------------------------------------- */
+
+/*
+ * Exact thresholds for K recurrence-rate targets per series (Sect. 2,
+ * "preselect RR and use the corresponding eps"; Eq. 3).
+ *   rr_num     host, K numerators, strictly ascending, each in 1..rr_den-1
+ *   rr_den     denominator (100 for RR in per cent)
+ *   eps_out    device, S*K FP32, row s = series s: eps_k is the T_k-th smallest
+ *              upper-triangle distance (non-decreasing in k)
+ *   count_le   device, S*K uint64: #{d <= eps_k} (may be NULL)
+ *   count_lt   device, S*K uint64: #{d < eps_k}  (may be NULL)
+ */
+int rqa_eps_for_rr(rqa_ctx *ctx, const rqa_batch *batch, const int32_t *rr_num,
+                   int32_t rr_den, int32_t K, float *eps_out, uint64_t *count_le,
+                   uint64_t *count_lt);
+
+/* Optional line outputs of rqa_det_avg (any member may be NULL). */
+typedef struct {
+    uint64_t *hist;               /* device, packed as in rqa_line_hist */
+    const int64_t *hist_offsets;  /* host, S+1, as in rqa_line_hist */
+    uint32_t *lmax;               /* device, S*K longest line */
+    uint64_t *count;              /* device, S*K recurrent cells C_k */
+    uint64_t *stencil;            /* device, S*K cells with a recurrent diagonal neighbour */
+} rqa_line_outputs;
+
+/*
+ * Determinism for each threshold and its average over the thresholds
+ * (Eq. 4 and Eq. avgDET) -- the whole hot path in one call when eps == NULL:
+ * threshold selection, then one pass over every cell that yields the counts,
+ * the line-length histogram and DET for all K thresholds at once.
+ *   eps        device, S*K FP32 thresholds, ascending within each series; or
+ *              NULL to select them first from rr_num/rr_den as rqa_eps_for_rr
+ *              does
+ *   rr_num     host, K numerators (read only when eps == NULL)
+ *   lmin       host, n_lmin (1..RQA_LMIN_MAX) minimal line lengths, each in
+ *              1..129 (paper: 2); DET_k(lmin) is NaN when C_k = 0
+ *   det_out    device, S*K*n_lmin FP64, [s][k][j] = DET_k(lmin[j]) (may be NULL)
+ *   det_avg    device, S*n_lmin FP64, [s][j] = (1/K) sum_k DET_k(lmin[j])
+ *   eps_used   device, S*K FP32 copy of the thresholds used (may be NULL)
+ *   lines      optional line outputs of the same pass (may be NULL)
+ */
+int rqa_det_avg(rqa_ctx *ctx, const rqa_batch *batch, const int32_t *rr_num,
+                int32_t rr_den, const float *eps, int32_t K, const int32_t *lmin,
+                int32_t n_lmin, double *det_out, double *det_avg, float *eps_used,
+                const rqa_line_outputs *lines);
+
+/*
+ * Full diagonal line-length histogram of the upper triangle (Eq. 4, Sect. 4).
+ *   eps          device, S*K FP32, ascending within each series
+ *   hist         device uint64, packed per series: series s occupies
+ *                hist[hist_offsets[s] .. hist_offsets[s+1]) laid out as
+ *                [k][l-1], l = 1..Ne_s-1, i.e. K*(Ne_s-1) entries; overwritten.
+ *                May be NULL (then hist_offsets is ignored).
+ *   hist_offsets host, S+1; hist_offsets[s+1]-hist_offsets[s] must equal
+ *                K*(Ne_s-1), else RQA_ERR_CAPACITY.
+ *   lmax         device, S*K uint32, longest line (may be NULL)
+ *   count        device, S*K uint64, recurrent cells C_k (may be NULL)
+ *   stencil      device, S*K uint64, recurrent cells with a recurrent diagonal
+ *                neighbour = C_k - P_k(1) (may be NULL)
+ */
+int rqa_line_hist(rqa_ctx *ctx, const rqa_batch *batch, const float *eps, int32_t K,
+                  uint64_t *hist, const int64_t *hist_offsets, uint32_t *lmax,
+                  uint64_t *count, uint64_t *stencil);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RQA_H */

@@ -1,0 +1,85 @@
+"""GB300-native averaged recurrence quantification analysis.
+
+For each delay-embedded FP32 series: exact thresholds eps_k for K target
+recurrence rates, determinism DET(eps_k) over the never-materialised
+recurrence matrix, its average over k, and the diagonal line-length histogram
+(Pánis, Adámek & Marwan, Sect. 2-4).  The work runs in hand-written sm_103a
+CUDA kernels behind a C ABI (``include/rqa.h``); this package is its Python
+binding (``abi``) plus a few conveniences that allocate outputs as tensors.
+"""
+from __future__ import annotations
+
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+from .abi import (  # noqa: F401
+    Batch, Context, RqaError, exported_symbols, lib,
+    rqa_abi_version, rqa_create, rqa_destroy, rqa_det_avg, rqa_device_info,
+    rqa_error_string, rqa_eps_for_rr, rqa_line_hist, rqa_status, rqa_target_counts,
+    rqa_set_timing, rqa_phase_times, rqa_kernel_launches,
+    RQA_SCHED_BATCHED, RQA_SCHED_PER_SERIES, RQA_SELECT_AUTO, RQA_SELECT_BRACKET,
+    RQA_SELECT_RADIX, RQA_K_MAX, RQA_LMIN_MAX, RQA_FEATURES,
+)
+
+
+def eps_for_rr(ctx: Context, batch: Batch, rr_num: Sequence[int], rr_den: int) -> Dict[str, "object"]:
+    """Thresholds and counts as CUDA tensors of shape (S, K)."""
+    import torch
+    S, K = batch.n_series, len(rr_num)
+    dev = batch.y.device
+    eps = torch.empty((S, K), dtype=torch.float32, device=dev)
+    le = torch.empty((S, K), dtype=torch.uint64, device=dev)
+    lt = torch.empty((S, K), dtype=torch.uint64, device=dev)
+    rqa_eps_for_rr(ctx, batch, rr_num, rr_den, eps, le, lt)
+    return {"eps": eps, "count_le": le, "count_lt": lt}
+
+
+def det_avg(ctx: Context, batch: Batch, rr_num: Optional[Sequence[int]], rr_den: int,
+            lmin: Sequence[int] = (2,), eps=None, K: Optional[int] = None,
+            lines: bool = False) -> Dict[str, "object"]:
+    """DET_k(lmin) (S, K, L), its mean over k (S, L) and the thresholds used;
+    with lines=True also the full histograms, L_max, C_k and stencil counts of
+    the same pass."""
+    import torch
+    S = batch.n_series
+    K = len(rr_num) if K is None else K
+    dev = batch.y.device
+    det = torch.empty((S, K, len(lmin)), dtype=torch.float64, device=dev)
+    avg = torch.empty((S, len(lmin)), dtype=torch.float64, device=dev)
+    used = torch.empty((S, K), dtype=torch.float32, device=dev)
+    out = {"det": det, "det_avg": avg, "eps": used}
+    if lines:
+        hoff = batch.hist_offsets(K)
+        out.update(hist=torch.empty(int(hoff[-1]), dtype=torch.uint64, device=dev), hist_offsets=hoff,
+                   lmax=torch.empty((S, K), dtype=torch.uint32, device=dev),
+                   count=torch.empty((S, K), dtype=torch.uint64, device=dev),
+                   stencil=torch.empty((S, K), dtype=torch.uint64, device=dev))
+        rqa_det_avg(ctx, batch, rr_num, rr_den, eps, K, lmin, det, avg, used, out["hist"], hoff,
+                    out["lmax"], out["count"], out["stencil"])
+    else:
+        rqa_det_avg(ctx, batch, rr_num, rr_den, eps, K, lmin, det, avg, used)
+    return out
+
+
+def line_hist(ctx: Context, batch: Batch, eps, K: int, full: bool = True) -> Dict[str, "object"]:
+    """Full P_k(l) histograms (packed per series), L_max, C_k and stencil counts."""
+    import torch
+    S = batch.n_series
+    dev = batch.y.device
+    hoff = batch.hist_offsets(K) if full else None
+    hist = torch.empty(int(hoff[-1]) if full else 0, dtype=torch.uint64, device=dev) if full else None
+    lmax = torch.empty((S, K), dtype=torch.uint32, device=dev)
+    cnt = torch.empty((S, K), dtype=torch.uint64, device=dev)
+    st = torch.empty((S, K), dtype=torch.uint64, device=dev)
+    rqa_line_hist(ctx, batch, eps, K, hist, hoff, lmax, cnt, st)
+    return {"hist": hist, "hist_offsets": hoff, "lmax": lmax, "count": cnt, "stencil": st}
+
+
+def unpack_hist(hist_np: np.ndarray, hoff: np.ndarray, batch: Batch, K: int):
+    """Split a packed histogram into per-series (K, Ne-1) arrays."""
+    out = []
+    for s in range(batch.n_series):
+        ne = int(batch.ne[s])
+        out.append(hist_np[hoff[s]:hoff[s + 1]].reshape(K, ne - 1))
+    return out

@@ -1,0 +1,292 @@
+"""Thin ctypes binding of ``librqa.so`` (the C ABI in ``include/rqa.h``).
+
+Only argument marshalling happens here: torch tensors supply device buffers
+and streams, NumPy arrays the host-side arrays.  Every step of the method runs
+in the library's CUDA kernels; there is no fallback, and loading fails loudly
+if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from .build import LIB
+
+c_int = ctypes.c_int
+c_i32 = ctypes.c_int32
+c_i64 = ctypes.c_int64
+c_u64 = ctypes.c_uint64
+c_vp = ctypes.c_void_p
+
+RQA_SCHED_BATCHED, RQA_SCHED_PER_SERIES = 0, 1
+RQA_SELECT_AUTO, RQA_SELECT_RADIX, RQA_SELECT_BRACKET = 0, 1, 2
+RQA_K_MAX = 31
+RQA_LMIN_MAX = 8
+RQA_FEATURES = 131
+
+
+class RqaError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {rqa_error_string(code)} (code {code})")
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("device", c_int), ("stream", c_vp), ("schedule", c_int), ("select", c_int),
+                ("band", c_int), ("blocks_per_sm", c_int), ("reserved", c_int * 4)]
+
+
+class _Batch(ctypes.Structure):
+    _fields_ = [("y", c_vp), ("offsets", c_vp), ("m", c_vp), ("tau", c_vp), ("n_series", c_i32)]
+
+
+class _LineOutputs(ctypes.Structure):
+    _fields_ = [("hist", c_vp), ("hist_offsets", c_vp), ("lmax", c_vp), ("count", c_vp),
+                ("stencil", c_vp)]
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+_SIGS = {
+    "rqa_abi_version": ([], c_int),
+    "rqa_error_string": ([c_int], ctypes.c_char_p),
+    "rqa_create": ([ctypes.POINTER(c_vp), ctypes.POINTER(_Config)], c_int),
+    "rqa_destroy": ([c_vp], None),
+    "rqa_status": ([c_vp], c_int),
+    "rqa_device_info": ([c_vp, c_vp, c_vp, c_vp], c_int),
+    "rqa_target_counts": ([c_u64, c_vp, c_i32, c_i32, c_vp], c_int),
+    "rqa_eps_for_rr": ([c_vp, ctypes.POINTER(_Batch), c_vp, c_i32, c_i32, c_vp, c_vp, c_vp], c_int),
+    "rqa_det_avg": ([c_vp, ctypes.POINTER(_Batch), c_vp, c_i32, c_vp, c_i32, c_vp, c_i32, c_vp,
+                     c_vp, c_vp, ctypes.POINTER(_LineOutputs)], c_int),
+    "rqa_set_timing": ([c_vp, c_int], c_int),
+    "rqa_phase_times": ([c_vp, c_vp, c_int], c_int),
+    "rqa_kernel_launches": ([c_vp], c_u64),
+    "rqa_line_hist": ([c_vp, ctypes.POINTER(_Batch), c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp],
+                      c_int),
+}
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def lib() -> ctypes.CDLL:
+    """Load librqa.so (built by ``build()``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"librqa.so is not built ({LIB}); run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def rqa_error_string(code: int) -> str:
+    try:
+        return lib().rqa_error_string(code).decode()
+    except Exception:
+        return "error"
+
+
+def rqa_abi_version() -> int:
+    return int(lib().rqa_abi_version())
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise RqaError(rc, where)
+
+
+def _np_ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(c_vp)
+
+
+def _dev_ptr(t, dtype, n: Optional[int] = None, name: str = "buffer"):
+    """Device pointer of a contiguous CUDA tensor of the given dtype (or None)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"{name} holds {t.numel()} elements, needs {n}")
+    return c_vp(t.data_ptr())
+
+
+class Batch:
+    """S series back to back in one CUDA FP32 tensor, with host metadata."""
+
+    def __init__(self, y, offsets, m, tau):
+        import torch
+        self.y = y
+        self.offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        S = len(self.offsets) - 1
+        self.m = np.ascontiguousarray(np.broadcast_to(np.asarray(m, dtype=np.int32), (S,)))
+        self.tau = np.ascontiguousarray(np.broadcast_to(np.asarray(tau, dtype=np.int32), (S,)))
+        if not isinstance(y, torch.Tensor) or not y.is_cuda or y.dtype != torch.float32:
+            raise TypeError("y must be a CUDA float32 tensor")
+        if not y.is_contiguous() or y.numel() < int(self.offsets[-1]):
+            raise ValueError("y must be contiguous and hold offsets[-1] values")
+
+    @property
+    def n_series(self) -> int:
+        return len(self.offsets) - 1
+
+    @property
+    def ne(self) -> np.ndarray:
+        n = np.diff(self.offsets)
+        return n - (self.m.astype(np.int64) - 1) * self.tau
+
+    def hist_offsets(self, K: int) -> np.ndarray:
+        off = np.zeros(self.n_series + 1, dtype=np.int64)
+        off[1:] = np.cumsum(K * (self.ne - 1))
+        return off
+
+    def _c(self) -> _Batch:
+        return _Batch(c_vp(self.y.data_ptr()), _np_ptr(self.offsets), _np_ptr(self.m),
+                      _np_ptr(self.tau), self.n_series)
+
+    @staticmethod
+    def from_numpy(series: Sequence[np.ndarray], m, tau, device: int = 0) -> "Batch":
+        import torch
+        offsets = np.zeros(len(series) + 1, dtype=np.int64)
+        offsets[1:] = np.cumsum([len(s) for s in series])
+        flat = np.concatenate([np.asarray(s, dtype=np.float32) for s in series])
+        y = torch.from_numpy(flat).to(f"cuda:{device}")
+        return Batch(y, offsets, m, tau)
+
+
+class Context:
+    """An ``rqa_ctx``: device, stream, schedule and scratch memory."""
+
+    def __init__(self, device: int = 0, stream=None, schedule: int = RQA_SCHED_BATCHED,
+                 select: int = RQA_SELECT_AUTO, band: int = 0, blocks_per_sm: int = 0):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        cfg = _Config(device, c_vp(handle), schedule, select, band, blocks_per_sm, (c_int * 4)())
+        p = c_vp()
+        _check(lib().rqa_create(ctypes.byref(p), ctypes.byref(cfg)), "rqa_create")
+        self._p = p
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._p
+
+    def close(self):
+        if getattr(self, "_p", None) is not None and self._p.value:
+            lib().rqa_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rqa_create(device: int = 0, stream=None, schedule: int = RQA_SCHED_BATCHED,
+               select: int = RQA_SELECT_AUTO, band: int = 0, blocks_per_sm: int = 0) -> Context:
+    return Context(device, stream, schedule, select, band, blocks_per_sm)
+
+
+def rqa_destroy(ctx: Context):
+    ctx.close()
+
+
+def rqa_status(ctx: Context) -> int:
+    return int(lib().rqa_status(ctx.handle))
+
+
+def rqa_device_info(ctx: Context):
+    sm, band, bpsm = c_int(), c_int(), c_int()
+    _check(lib().rqa_device_info(ctx.handle, ctypes.byref(sm), ctypes.byref(band),
+                                 ctypes.byref(bpsm)), "rqa_device_info")
+    return {"sm_count": sm.value, "band": band.value, "blocks_per_sm": bpsm.value}
+
+
+def rqa_target_counts(P: int, rr_num: Sequence[int], rr_den: int) -> np.ndarray:
+    rr = np.ascontiguousarray(rr_num, dtype=np.int32)
+    out = np.zeros(len(rr), dtype=np.uint64)
+    _check(lib().rqa_target_counts(int(P), _np_ptr(rr), int(rr_den), len(rr), _np_ptr(out)),
+           "rqa_target_counts")
+    return out
+
+
+def rqa_eps_for_rr(ctx: Context, batch: Batch, rr_num, rr_den: int, eps_out, count_le=None,
+                   count_lt=None):
+    import torch
+    rr = np.ascontiguousarray(rr_num, dtype=np.int32)
+    n = batch.n_series * len(rr)
+    b = batch._c()
+    _check(lib().rqa_eps_for_rr(ctx.handle, ctypes.byref(b), _np_ptr(rr), int(rr_den), len(rr),
+                                _dev_ptr(eps_out, torch.float32, n, "eps_out"),
+                                _dev_ptr(count_le, torch.uint64, n, "count_le"),
+                                _dev_ptr(count_lt, torch.uint64, n, "count_lt")), "rqa_eps_for_rr")
+
+
+def rqa_det_avg(ctx: Context, batch: Batch, rr_num, rr_den: int, eps, K: int, lmin, det_out,
+                det_avg, eps_used=None, hist=None, hist_offsets=None, lmax=None, count=None,
+                stencil=None):
+    import torch
+    rr = None if rr_num is None else np.ascontiguousarray(rr_num, dtype=np.int32)
+    lm = np.ascontiguousarray(lmin, dtype=np.int32)
+    S = batch.n_series
+    b = batch._c()
+    hoff = None if hist_offsets is None else np.ascontiguousarray(hist_offsets, dtype=np.int64)
+    lo = None
+    if any(v is not None for v in (hist, lmax, count, stencil)):
+        lo = _LineOutputs(_dev_ptr(hist, torch.uint64, None if hoff is None else int(hoff[-1]), "hist"),
+                          _np_ptr(hoff), _dev_ptr(lmax, torch.uint32, S * K, "lmax"),
+                          _dev_ptr(count, torch.uint64, S * K, "count"),
+                          _dev_ptr(stencil, torch.uint64, S * K, "stencil"))
+    _check(lib().rqa_det_avg(ctx.handle, ctypes.byref(b), _np_ptr(rr), int(rr_den),
+                             _dev_ptr(eps, torch.float32, S * K, "eps"), int(K), _np_ptr(lm),
+                             len(lm), _dev_ptr(det_out, torch.float64, S * K * len(lm), "det_out"),
+                             _dev_ptr(det_avg, torch.float64, S * len(lm), "det_avg"),
+                             _dev_ptr(eps_used, torch.float32, S * K, "eps_used"),
+                             None if lo is None else ctypes.byref(lo)), "rqa_det_avg")
+
+
+def rqa_set_timing(ctx: Context, enable: bool = True):
+    _check(lib().rqa_set_timing(ctx.handle, int(bool(enable))), "rqa_set_timing")
+
+
+def rqa_phase_times(ctx: Context) -> np.ndarray:
+    out = np.zeros(6, dtype=np.float32)
+    _check(lib().rqa_phase_times(ctx.handle, _np_ptr(out), 6), "rqa_phase_times")
+    return out
+
+
+def rqa_kernel_launches(ctx: Context) -> int:
+    return int(lib().rqa_kernel_launches(ctx.handle))
+
+
+def rqa_line_hist(ctx: Context, batch: Batch, eps, K: int, hist=None, hist_offsets=None,
+                  lmax=None, count=None, stencil=None):
+    import torch
+    S = batch.n_series
+    hoff = None if hist_offsets is None else np.ascontiguousarray(hist_offsets, dtype=np.int64)
+    b = batch._c()
+    _check(lib().rqa_line_hist(ctx.handle, ctypes.byref(b), _dev_ptr(eps, torch.float32, S * K, "eps"),
+                               int(K),
+                               _dev_ptr(hist, torch.uint64, None if hoff is None else int(hoff[-1]),
+                                        "hist"),
+                               _np_ptr(hoff), _dev_ptr(lmax, torch.uint32, S * K, "lmax"),
+                               _dev_ptr(count, torch.uint64, S * K, "count"),
+                               _dev_ptr(stencil, torch.uint64, S * K, "stencil")), "rqa_line_hist")

@@ -1,0 +1,713 @@
+// Host side of librqa: argument validation, work planning and the launch
+// sequences behind the C ABI declared in include/rqa.h.
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "rqa.h"
+#include "rqa_internal.h"
+
+using namespace rqa;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+int ensure(DevBuf &b, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (bytes <= b.cap) return RQA_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return RQA_ERR_OOM;
+    }
+    b.cap = bytes;
+    return RQA_OK;
+}
+
+template <class T>
+T *P(DevBuf &b) { return reinterpret_cast<T *>(b.p); }
+
+size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+}  // namespace
+
+struct rqa_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int schedule = RQA_SCHED_BATCHED;
+    int select = RQA_SELECT_AUTO;
+    int band = 16;
+    int bpsm = 0;
+    int sm_count = 0;
+
+    // scratch (grow-only)
+    DevBuf arena;      // uploaded plan: series, targets, items, lmin, hist offsets
+    DevBuf prefix, level, rank, below, tab_sub, tab_mid, tab_fin1, tab_fin2, ngroups, hist;
+    DevBuf queue, status;
+    DevBuf eps_tmp, le_tmp, lt_tmp, count, lmax, hshort;
+
+    // per-phase timing of the last call (batched schedule)
+    bool timing = false;
+    cudaEvent_t ev[7] = {};
+    bool ev_recorded = false;
+    uint64_t launches = 0;
+
+    // pinned host staging of the plan upload
+    void *h_stage = nullptr;
+    size_t h_cap = 0;
+    cudaEvent_t stage_done = nullptr;
+    bool stage_pending = false;
+};
+
+namespace {
+
+struct Plan {
+    int S = 0, K = 0;
+    int mt = 0;                 // common embedding dimension if <= 4, else 0
+    int64_t total = 0;          // values in the batch buffer
+    std::vector<SeriesDev> sd;
+    std::vector<uint64_t> T;    // S*K (empty if no targets)
+    std::vector<Item> items_lpt;             // whole batch, largest first
+    std::vector<Item> items_ser;             // grouped by series
+    std::vector<int> ser_begin;              // S+1 into items_ser
+    // device pointers into the arena after upload
+    SeriesDev *d_sd = nullptr;
+    uint64_t *d_T = nullptr;
+    Item *d_lpt = nullptr;
+    Item *d_ser = nullptr;
+    int32_t *d_lmin = nullptr;
+    int64_t *d_hoff = nullptr;
+};
+
+int check_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return RQA_OK;
+    cudaGetLastError();
+    return RQA_ERR_CUDA;
+}
+
+// A kernel launch through one of the launch wrappers: counted per context.
+int launched(rqa_ctx *c, cudaError_t e)
+{
+    c->launches++;
+    return check_cuda(e);
+}
+
+// Phase boundary i (0..6) of the timed sequence.
+void mark(rqa_ctx *c, int i)
+{
+    if (c->timing && c->schedule == RQA_SCHED_BATCHED) {
+        cudaEventRecord(c->ev[i], c->stream);
+        if (i == 6) c->ev_recorded = true;
+    }
+}
+
+uint64_t band_cost(int64_t ne, int64_t d_lo, int64_t d_hi)
+{
+    // sum_{delta = d_lo}^{d_hi - 1} (ne - delta)
+    const int64_t n = d_hi - d_lo;
+    return (uint64_t)(n * ne - (d_lo + d_hi - 1) * n / 2);
+}
+
+void build_items(const SeriesDev &s, int sidx, int band, uint64_t target, std::vector<Item> &out,
+                 std::vector<uint64_t> *costs)
+{
+    Item cur{sidx, 0, 0, 0};
+    uint64_t acc = 0;
+    for (int b = 0; b < s.nbands; ++b) {
+        const int64_t d_lo = 1 + (int64_t)b * band;
+        const int64_t d_hi = std::min<int64_t>(d_lo + band, s.ne);
+        acc += band_cost(s.ne, d_lo, d_hi);
+        cur.b_hi = b + 1;
+        if (acc >= target || b + 1 == s.nbands) {
+            out.push_back(cur);
+            if (costs) costs->push_back(acc);
+            cur.b_lo = b + 1;
+            acc = 0;
+        }
+    }
+}
+
+int validate_batch(const rqa_batch *b)
+{
+    if (!b || !b->y || !b->offsets || !b->m || !b->tau || b->n_series < 1)
+        return RQA_ERR_INVALID_ARG;
+    if (b->offsets[0] != 0) return RQA_ERR_INVALID_ARG;
+    for (int s = 0; s < b->n_series; ++s) {
+        const int64_t n = b->offsets[s + 1] - b->offsets[s];
+        if (n < 0) return RQA_ERR_INVALID_ARG;
+        if (b->m[s] < 1 || b->m[s] > RQA_M_MAX || b->tau[s] < 1) return RQA_ERR_INVALID_ARG;
+        if (n > (int64_t)0x7fffffff - 64) return RQA_ERR_CAPACITY;
+        const int64_t ne = n - (int64_t)(b->m[s] - 1) * b->tau[s];
+        if (ne < 2) return RQA_ERR_TOO_SHORT;
+    }
+    return RQA_OK;
+}
+
+int validate_rr(const int32_t *rr_num, int32_t rr_den, int32_t K)
+{
+    if (!rr_num || K < 1 || K > RQA_K_MAX || rr_den < 2) return RQA_ERR_INVALID_ARG;
+    for (int k = 0; k < K; ++k) {
+        if (rr_num[k] < 1 || rr_num[k] >= rr_den) return RQA_ERR_INVALID_ARG;
+        if (k && rr_num[k] <= rr_num[k - 1]) return RQA_ERR_INVALID_ARG;
+    }
+    return RQA_OK;
+}
+
+int make_plan(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_den, int K,
+              Plan &pl)
+{
+    const int S = b->n_series;
+    pl.S = S;
+    pl.K = K;
+    pl.sd.resize(S);
+    int m0 = b->m[0];
+    bool uniform = true;
+    uint64_t total_cells = 0;
+    for (int s = 0; s < S; ++s) {
+        SeriesDev &d = pl.sd[s];
+        d.off = b->offsets[s];
+        d.n = (int32_t)(b->offsets[s + 1] - b->offsets[s]);
+        d.m = b->m[s];
+        d.tau = b->tau[s];
+        d.ne = d.n - (d.m - 1) * d.tau;
+        d.P = (uint64_t)d.ne * (uint64_t)(d.ne - 1) / 2;
+        d.nbands = (d.ne - 1 + c->band - 1) / c->band;
+        d.pad = 0;
+        uniform &= (d.m == m0);
+        total_cells += d.P;
+    }
+    pl.total = b->offsets[S];
+    pl.mt = (uniform && m0 <= 4) ? m0 : 0;
+    if (rr_num) {
+        pl.T.resize((size_t)S * K);
+        for (int s = 0; s < S; ++s)
+            if (rqa_target_counts(pl.sd[s].P, rr_num, rr_den, K, &pl.T[(size_t)s * K]) != RQA_OK)
+                return RQA_ERR_INVALID_ARG;
+    }
+    // Work items: runs of consecutive bands of one series.  Batched: sized so
+    // that every SM gets several, then sorted largest first (the persistent
+    // CTAs take them in that order).  Per series: sized from the series alone.
+    const uint64_t workers = (uint64_t)c->sm_count * 4;
+    const uint64_t cap = (uint64_t)1 << 30;  // keeps 32-bit shared counters exact
+    uint64_t tgt = std::max<uint64_t>(total_cells / (workers * 4), (uint64_t)1 << 15);
+    tgt = std::min(tgt, cap);
+    std::vector<Item> items;
+    std::vector<uint64_t> costs;
+    for (int s = 0; s < S; ++s) build_items(pl.sd[s], s, c->band, tgt, items, &costs);
+    std::vector<size_t> order(items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t x, size_t y) { return costs[x] > costs[y]; });
+    pl.items_lpt.resize(items.size());
+    for (size_t i = 0; i < order.size(); ++i) pl.items_lpt[i] = items[order[i]];
+    pl.ser_begin.assign(S + 1, 0);
+    for (int s = 0; s < S; ++s) {
+        uint64_t t = std::max<uint64_t>(pl.sd[s].P / (workers * 4), (uint64_t)1 << 13);
+        t = std::min(t, cap);
+        build_items(pl.sd[s], s, c->band, t, pl.items_ser, nullptr);
+        pl.ser_begin[s + 1] = (int)pl.items_ser.size();
+    }
+    return RQA_OK;
+}
+
+// Copy the plan (and optional lmin list / histogram offsets) to the device.
+int upload_plan(rqa_ctx *c, Plan &pl, const int32_t *lmin, int n_lmin, const int64_t *hoff)
+{
+    const size_t o_sd = 0;
+    const size_t o_T = align16(o_sd + pl.sd.size() * sizeof(SeriesDev));
+    const size_t o_lpt = align16(o_T + pl.T.size() * sizeof(uint64_t));
+    const size_t o_ser = align16(o_lpt + pl.items_lpt.size() * sizeof(Item));
+    const size_t o_lmin = align16(o_ser + pl.items_ser.size() * sizeof(Item));
+    const size_t o_hoff = align16(o_lmin + (size_t)n_lmin * sizeof(int32_t));
+    const size_t total = align16(o_hoff + (hoff ? (size_t)(pl.S + 1) * sizeof(int64_t) : 0));
+
+    if (c->stage_pending) {
+        if (cudaEventSynchronize(c->stage_done) != cudaSuccess) return check_cuda(cudaGetLastError());
+        c->stage_pending = false;
+    }
+    if (total > c->h_cap) {
+        if (c->h_stage) cudaFreeHost(c->h_stage);
+        c->h_stage = nullptr;
+        c->h_cap = 0;
+        if (cudaHostAlloc(&c->h_stage, total, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return RQA_ERR_OOM;
+        }
+        c->h_cap = total;
+    }
+    if (int rc = ensure(c->arena, total)) return rc;
+    char *h = static_cast<char *>(c->h_stage);
+    std::memcpy(h + o_sd, pl.sd.data(), pl.sd.size() * sizeof(SeriesDev));
+    if (!pl.T.empty()) std::memcpy(h + o_T, pl.T.data(), pl.T.size() * sizeof(uint64_t));
+    std::memcpy(h + o_lpt, pl.items_lpt.data(), pl.items_lpt.size() * sizeof(Item));
+    std::memcpy(h + o_ser, pl.items_ser.data(), pl.items_ser.size() * sizeof(Item));
+    if (n_lmin) std::memcpy(h + o_lmin, lmin, (size_t)n_lmin * sizeof(int32_t));
+    if (hoff) std::memcpy(h + o_hoff, hoff, (size_t)(pl.S + 1) * sizeof(int64_t));
+    char *d = static_cast<char *>(c->arena.p);
+    if (int rc = check_cuda(cudaMemcpyAsync(d, h, total, cudaMemcpyHostToDevice, c->stream))) return rc;
+    if (int rc = check_cuda(cudaEventRecord(c->stage_done, c->stream))) return rc;
+    c->stage_pending = true;
+    pl.d_sd = reinterpret_cast<SeriesDev *>(d + o_sd);
+    pl.d_T = reinterpret_cast<uint64_t *>(d + o_T);
+    pl.d_lpt = reinterpret_cast<Item *>(d + o_lpt);
+    pl.d_ser = reinterpret_cast<Item *>(d + o_ser);
+    pl.d_lmin = reinterpret_cast<int32_t *>(d + o_lmin);
+    pl.d_hoff = reinterpret_cast<int64_t *>(d + o_hoff);
+    return RQA_OK;
+}
+
+int64_t hist_stride(int K) { return NCOARSE + (int64_t)std::max(K, NSUB_MAX) * NFINE; }
+
+int ensure_select_bufs(rqa_ctx *c, int S, int K)
+{
+    const size_t sk = (size_t)S * K;
+    int rc = RQA_OK;
+    if ((rc = ensure(c->prefix, sk * 4))) return rc;
+    if ((rc = ensure(c->level, sk))) return rc;
+    if ((rc = ensure(c->rank, sk * 8))) return rc;
+    if ((rc = ensure(c->below, sk * 8))) return rc;
+    if ((rc = ensure(c->tab_sub, (size_t)S * NCOARSE))) return rc;
+    if ((rc = ensure(c->tab_mid, (size_t)S * NCOARSE))) return rc;
+    if ((rc = ensure(c->tab_fin1, (size_t)S * NCOARSE))) return rc;
+    if ((rc = ensure(c->tab_fin2, (size_t)S * KMAX * NFINE))) return rc;
+    if ((rc = ensure(c->ngroups, (size_t)S * 4 * sizeof(int32_t)))) return rc;
+    if ((rc = ensure(c->hist, (size_t)S * hist_stride(K) * 8))) return rc;
+    if ((rc = ensure(c->eps_tmp, sk * 4))) return rc;
+    if ((rc = ensure(c->le_tmp, sk * 8))) return rc;
+    if ((rc = ensure(c->lt_tmp, sk * 8))) return rc;
+    return RQA_OK;
+}
+
+SelBufs sel_bufs(rqa_ctx *c, const Plan &pl)
+{
+    SelBufs sb;
+    sb.T = pl.d_T;
+    sb.prefix = P<uint32_t>(c->prefix);
+    sb.level = P<uint8_t>(c->level);
+    sb.rank = P<uint64_t>(c->rank);
+    sb.below = P<uint64_t>(c->below);
+    sb.tab_sub = P<int8_t>(c->tab_sub);
+    sb.tab_mid = P<int8_t>(c->tab_mid);
+    sb.tab_fin1 = P<int8_t>(c->tab_fin1);
+    sb.tab_fin2 = P<int8_t>(c->tab_fin2);
+    int32_t *ng = P<int32_t>(c->ngroups);
+    sb.n_sub = ng;
+    sb.n_mid = ng + pl.S;
+    sb.n_fin = ng + 2 * pl.S;
+    sb.hist = P<uint64_t>(c->hist);
+    sb.hstride = hist_stride(pl.K);
+    return sb;
+}
+
+int persistent_grid(rqa_ctx *c, size_t n_items)
+{
+    const int bpsm = c->bpsm > 0 ? c->bpsm : 2;
+    const size_t g = (size_t)c->sm_count * bpsm;
+    return (int)std::max<size_t>(1, std::min(g, n_items));
+}
+
+// Zero the queue tickets of n launches; returns the first ticket pointer.
+int reset_queue(rqa_ctx *c, int n, unsigned **q)
+{
+    if (int rc = ensure(c->queue, (size_t)n * 64)) return rc;
+    if (int rc = check_cuda(cudaMemsetAsync(c->queue.p, 0, (size_t)n * 64, c->stream))) return rc;
+    *q = P<unsigned>(c->queue);
+    return RQA_OK;
+}
+
+// Radix selection for series [s0, s0+ns) using the given item list.
+int run_select(rqa_ctx *c, const Plan &pl, const SelBufs &sb, const Item *items, int n_items,
+               int s0, int ns, unsigned *&q, float *eps, uint64_t *le, uint64_t *lt)
+{
+    const int K = pl.K;
+    const int grid = persistent_grid(c, (size_t)n_items);
+    CellArgs a;
+    a.series = pl.d_sd;
+    a.items = items;
+    a.n_items = n_items;
+    a.band = c->band;
+    a.status = P<int>(c->status);
+    const size_t hbytes = (size_t)ns * sb.hstride * 8;
+    uint64_t *hbase = sb.hist + (int64_t)s0 * sb.hstride;
+    const int rounds[3] = {R_COARSE, R_MID, R_FINAL};
+    for (int r = 0; r < 3; ++r) {
+        if (int rc = check_cuda(cudaMemsetAsync(hbase, 0, hbytes, c->stream))) return rc;
+        a.queue = q;
+        q += 16;
+        if (int rc = launched(c, launch_count(rounds[r], a, sb, K, grid, pl.mt, c->stream))) return rc;
+        if (int rc = launched(c, launch_select(rounds[r], sb, pl.d_sd, s0, ns, K, eps, le, lt,
+                                               P<int>(c->status), c->stream)))
+            return rc;
+        mark(c, 2 + r);
+    }
+    return RQA_OK;
+}
+
+int select_all(rqa_ctx *c, const rqa_batch *b, Plan &pl, float *eps, uint64_t *le, uint64_t *lt)
+{
+    const SelBufs sb = sel_bufs(c, pl);
+    mark(c, 0);
+    if (int rc = launched(c, launch_check_finite(b->y, pl.total, P<int>(c->status), c->stream)))
+        return rc;
+    mark(c, 1);
+    if (int rc = check_cuda(cudaMemsetAsync(c->ngroups.p, 0, (size_t)pl.S * 4 * sizeof(int32_t),
+                                            c->stream)))
+        return rc;
+    unsigned *q = nullptr;
+    if (c->schedule == RQA_SCHED_PER_SERIES) {
+        if (int rc = reset_queue(c, 3 * pl.S, &q)) return rc;
+        for (int s = 0; s < pl.S; ++s) {
+            const int ib = pl.ser_begin[s], ie = pl.ser_begin[s + 1];
+            if (int rc = run_select(c, pl, sb, pl.d_ser + ib, ie - ib, s, 1, q, eps, le, lt))
+                return rc;
+        }
+        return RQA_OK;
+    }
+    if (int rc = reset_queue(c, 3, &q)) return rc;
+    return run_select(c, pl, sb, pl.d_lpt, (int)pl.items_lpt.size(), 0, pl.S, q, eps, le, lt);
+}
+
+int ensure_line_bufs(rqa_ctx *c, int S, int K)
+{
+    const size_t sk = (size_t)S * K;
+    int rc = RQA_OK;
+    if ((rc = ensure(c->count, sk * 8))) return rc;
+    if ((rc = ensure(c->lmax, sk * 4))) return rc;
+    if ((rc = ensure(c->hshort, sk * LSH * 8))) return rc;
+    return RQA_OK;
+}
+
+// The line pass over every series; fills count / lmax / hshort (and hist).
+int run_lines(rqa_ctx *c, const Plan &pl, const float *eps, uint64_t *hist, const int64_t *d_hoff,
+              LineBufs &lb)
+{
+    const int S = pl.S, K = pl.K;
+    const size_t sk = (size_t)S * K;
+    lb.eps = eps;
+    lb.count = P<uint64_t>(c->count);
+    lb.lmax = P<uint32_t>(c->lmax);
+    lb.hshort = P<uint64_t>(c->hshort);
+    lb.hist = hist;
+    lb.hist_off = d_hoff;
+    if (int rc = check_cuda(cudaMemsetAsync(lb.count, 0, sk * 8, c->stream))) return rc;
+    if (int rc = check_cuda(cudaMemsetAsync(lb.lmax, 0, sk * 4, c->stream))) return rc;
+    if (int rc = check_cuda(cudaMemsetAsync(lb.hshort, 0, sk * LSH * 8, c->stream))) return rc;
+    CellArgs a;
+    a.series = pl.d_sd;
+    a.band = c->band;
+    a.status = P<int>(c->status);
+    unsigned *q = nullptr;
+    if (c->schedule == RQA_SCHED_PER_SERIES) {
+        if (int rc = reset_queue(c, S, &q)) return rc;
+        for (int s = 0; s < S; ++s) {
+            const int ib = pl.ser_begin[s], ie = pl.ser_begin[s + 1];
+            a.items = pl.d_ser + ib;
+            a.n_items = ie - ib;
+            a.queue = q;
+            q += 16;
+            if (int rc = launched(c, launch_lines(a, lb, K, persistent_grid(c, (size_t)a.n_items),
+                                                  pl.mt, c->stream)))
+                return rc;
+        }
+        return RQA_OK;
+    }
+    if (int rc = reset_queue(c, 1, &q)) return rc;
+    a.items = pl.d_lpt;
+    a.n_items = (int)pl.items_lpt.size();
+    a.queue = q;
+    return launched(c, launch_lines(a, lb, K, persistent_grid(c, (size_t)a.n_items), pl.mt, c->stream));
+}
+
+// Line pass plus the requested outputs.  hist/hoff come from the caller.
+int lines_and_outputs(rqa_ctx *c, const Plan &pl, const float *eps, const rqa_line_outputs *lo,
+                      LineBufs &lb)
+{
+    uint64_t *hist = lo ? lo->hist : nullptr;
+    if (hist)
+        if (int rc = check_cuda(cudaMemsetAsync(hist, 0, (size_t)lo->hist_offsets[pl.S] * 8, c->stream)))
+            return rc;
+    if (int rc = run_lines(c, pl, eps, hist, hist ? pl.d_hoff : nullptr, lb)) return rc;
+    mark(c, 5);
+    return RQA_OK;
+}
+
+int line_outputs_tail(rqa_ctx *c, const Plan &pl, const rqa_line_outputs *lo, LineBufs &lb)
+{
+    if (!lo) return RQA_OK;
+    const size_t sk = (size_t)pl.S * pl.K;
+    if (lo->hist || lo->stencil)
+        if (int rc = launched(c, launch_finalize_hist(lb, pl.d_sd, pl.S, pl.K, lo->stencil, c->stream)))
+            return rc;
+    if (lo->lmax)
+        if (int rc = check_cuda(cudaMemcpyAsync(lo->lmax, lb.lmax, sk * 4, cudaMemcpyDeviceToDevice,
+                                                c->stream)))
+            return rc;
+    if (lo->count)
+        if (int rc = check_cuda(cudaMemcpyAsync(lo->count, lb.count, sk * 8, cudaMemcpyDeviceToDevice,
+                                                c->stream)))
+            return rc;
+    return RQA_OK;
+}
+
+int validate_hist(const rqa_batch *b, int K, const uint64_t *hist, const int64_t *hoff)
+{
+    if (!hist) return RQA_OK;
+    if (!hoff) return RQA_ERR_INVALID_ARG;
+    if (hoff[0] != 0) return RQA_ERR_CAPACITY;
+    for (int s = 0; s < b->n_series; ++s) {
+        const int64_t ne = (b->offsets[s + 1] - b->offsets[s]) - (int64_t)(b->m[s] - 1) * b->tau[s];
+        if (hoff[s + 1] - hoff[s] != (int64_t)K * (ne - 1)) return RQA_ERR_CAPACITY;
+    }
+    return RQA_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+int rqa_abi_version(void) { return RQA_ABI_VERSION; }
+
+const char *rqa_error_string(int code)
+{
+    switch (code) {
+    case RQA_OK: return "ok";
+    case RQA_ERR_INVALID_ARG: return "invalid argument";
+    case RQA_ERR_TOO_SHORT: return "series too short (fewer than two embedded vectors)";
+    case RQA_ERR_NONFINITE: return "series holds a non-finite value";
+    case RQA_ERR_CUDA: return "CUDA runtime error";
+    case RQA_ERR_OOM: return "out of device or pinned host memory";
+    case RQA_ERR_TIMEOUT: return "a bounded device wait timed out";
+    case RQA_ERR_CAPACITY: return "buffer too small or size limit exceeded";
+    case RQA_ERR_UNSORTED: return "thresholds not ascending, negative or NaN";
+    case RQA_ERR_NO_MODEL: return "bracket selection requested without a model";
+    case RQA_ERR_INTERNAL: return "internal inconsistency in device counts";
+    default: return "unknown error";
+    }
+}
+
+int rqa_target_counts(uint64_t Pc, const int32_t *rr_num, int32_t rr_den, int32_t K,
+                      uint64_t *T_out)
+{
+    if (!rr_num || !T_out || K < 1 || rr_den < 1 || Pc < 1) return RQA_ERR_INVALID_ARG;
+    for (int k = 0; k < K; ++k) {
+        if (rr_num[k] < 1 || rr_num[k] >= rr_den) return RQA_ERR_INVALID_ARG;
+        const unsigned __int128 num = (unsigned __int128)(uint64_t)rr_num[k] * Pc;
+        const unsigned __int128 t = (num + (unsigned __int128)(rr_den - 1)) / (unsigned)rr_den;
+        T_out[k] = (uint64_t)t;
+    }
+    return RQA_OK;
+}
+
+int rqa_create(rqa_ctx **out, const rqa_config *cfg)
+{
+    if (!out) return RQA_ERR_INVALID_ARG;
+    *out = nullptr;
+    rqa_config def;
+    std::memset(&def, 0, sizeof(def));
+    if (!cfg) cfg = &def;
+    for (int i = 0; i < 4; ++i)
+        if (cfg->reserved[i]) return RQA_ERR_INVALID_ARG;
+    if (cfg->schedule != RQA_SCHED_BATCHED && cfg->schedule != RQA_SCHED_PER_SERIES)
+        return RQA_ERR_INVALID_ARG;
+    if (cfg->select < RQA_SELECT_AUTO || cfg->select > RQA_SELECT_BRACKET) return RQA_ERR_INVALID_ARG;
+    if (cfg->band != 0 && cfg->band != 16) return RQA_ERR_INVALID_ARG;
+    if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 8) return RQA_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+        cudaGetLastError();
+        return RQA_ERR_CUDA;
+    }
+    if (cudaSetDevice(cfg->device) != cudaSuccess) return check_cuda(cudaGetLastError());
+    rqa_ctx *c = new (std::nothrow) rqa_ctx;
+    if (!c) return RQA_ERR_OOM;
+    c->device = cfg->device;
+    c->stream = static_cast<cudaStream_t>(cfg->stream);
+    c->schedule = cfg->schedule;
+    c->select = cfg->select;
+    c->band = cfg->band ? cfg->band : 16;
+    c->bpsm = cfg->blocks_per_sm;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return RQA_ERR_CUDA;
+    }
+    c->sm_count = prop.multiProcessorCount;
+    if (ensure(c->status, 64) != RQA_OK || cudaMemset(c->status.p, 0, 64) != cudaSuccess) {
+        cudaGetLastError();
+        rqa_destroy(c);
+        return RQA_ERR_OOM;
+    }
+    *out = c;
+    return RQA_OK;
+}
+
+void rqa_destroy(rqa_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    DevBuf *bufs[] = {&c->arena, &c->prefix, &c->level, &c->rank, &c->below, &c->tab_sub,
+                      &c->tab_mid, &c->tab_fin1, &c->tab_fin2, &c->ngroups, &c->hist, &c->queue,
+                      &c->status, &c->eps_tmp, &c->le_tmp, &c->lt_tmp, &c->count, &c->lmax,
+                      &c->hshort};
+    for (DevBuf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->stage_done) cudaEventDestroy(c->stage_done);
+    for (int i = 0; i < 7; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    cudaGetLastError();
+    delete c;
+}
+
+int rqa_status(rqa_ctx *c)
+{
+    if (!c) return RQA_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(cudaGetLastError());
+    int st = 0;
+    if (cudaMemcpy(&st, c->status.p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return check_cuda(cudaGetLastError());
+    if (st) cudaMemset(c->status.p, 0, sizeof(int));
+    return st;
+}
+
+int rqa_device_info(rqa_ctx *c, int *sm_count, int *band, int *blocks_per_sm)
+{
+    if (!c) return RQA_ERR_INVALID_ARG;
+    if (sm_count) *sm_count = c->sm_count;
+    if (band) *band = c->band;
+    if (blocks_per_sm) *blocks_per_sm = c->bpsm > 0 ? c->bpsm : 2;
+    return RQA_OK;
+}
+
+int rqa_eps_for_rr(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_den,
+                   int32_t K, float *eps_out, uint64_t *count_le, uint64_t *count_lt)
+{
+    if (!c || !eps_out) return RQA_ERR_INVALID_ARG;
+    if (int rc = validate_batch(b)) return rc;
+    if (int rc = validate_rr(rr_num, rr_den, K)) return rc;
+    if (c->select == RQA_SELECT_BRACKET) return RQA_ERR_NO_MODEL;
+    cudaSetDevice(c->device);
+    Plan pl;
+    if (int rc = make_plan(c, b, rr_num, rr_den, K, pl)) return rc;
+    if (int rc = ensure_select_bufs(c, pl.S, K)) return rc;
+    if (int rc = upload_plan(c, pl, nullptr, 0, nullptr)) return rc;
+    return select_all(c, b, pl, eps_out, count_le, count_lt);
+}
+
+int rqa_det_avg(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_den,
+                const float *eps, int32_t K, const int32_t *lmin, int32_t n_lmin, double *det_out,
+                double *det_avg, float *eps_used, const rqa_line_outputs *lo)
+{
+    if (!c || !det_avg || !lmin || n_lmin < 1 || n_lmin > RQA_LMIN_MAX) return RQA_ERR_INVALID_ARG;
+    if (K < 1 || K > RQA_K_MAX) return RQA_ERR_INVALID_ARG;
+    for (int j = 0; j < n_lmin; ++j)
+        if (lmin[j] < 1 || lmin[j] > LSH + 1) return RQA_ERR_INVALID_ARG;
+    if (int rc = validate_batch(b)) return rc;
+    if (lo)
+        if (int rc = validate_hist(b, K, lo->hist, lo->hist_offsets)) return rc;
+    if (!eps) {
+        if (int rc = validate_rr(rr_num, rr_den, K)) return rc;
+        if (c->select == RQA_SELECT_BRACKET) return RQA_ERR_NO_MODEL;
+    }
+    cudaSetDevice(c->device);
+    Plan pl;
+    if (int rc = make_plan(c, b, eps ? nullptr : rr_num, rr_den, K, pl)) return rc;
+    if (int rc = ensure_line_bufs(c, pl.S, K)) return rc;
+    if (!eps)
+        if (int rc = ensure_select_bufs(c, pl.S, K)) return rc;
+    const int64_t *hoff = (lo && lo->hist) ? lo->hist_offsets : nullptr;
+    if (int rc = upload_plan(c, pl, lmin, n_lmin, hoff)) return rc;
+    const float *e = eps;
+    if (!eps) {
+        if (int rc = select_all(c, b, pl, P<float>(c->eps_tmp), P<uint64_t>(c->le_tmp),
+                                P<uint64_t>(c->lt_tmp)))
+            return rc;
+        e = P<float>(c->eps_tmp);
+    } else {
+        mark(c, 0);
+        if (int rc = launched(c, launch_check_finite(b->y, pl.total, P<int>(c->status), c->stream)))
+            return rc;
+        for (int i = 1; i <= 4; ++i) mark(c, i);
+    }
+    LineBufs lb;
+    if (int rc = lines_and_outputs(c, pl, e, lo, lb)) return rc;
+    if (int rc = launched(c, launch_finalize_det(lb, pl.d_sd, pl.S, K, pl.d_lmin, n_lmin, det_out,
+                                                 det_avg, c->stream)))
+        return rc;
+    if (int rc = line_outputs_tail(c, pl, lo, lb)) return rc;
+    mark(c, 6);
+    if (eps_used)
+        if (int rc = check_cuda(cudaMemcpyAsync(eps_used, e, (size_t)pl.S * K * 4,
+                                                cudaMemcpyDeviceToDevice, c->stream)))
+            return rc;
+    return RQA_OK;
+}
+
+int rqa_line_hist(rqa_ctx *c, const rqa_batch *b, const float *eps, int32_t K, uint64_t *hist,
+                  const int64_t *hist_offsets, uint32_t *lmax, uint64_t *count, uint64_t *stencil)
+{
+    if (!c || !eps || K < 1 || K > RQA_K_MAX) return RQA_ERR_INVALID_ARG;
+    if (int rc = validate_batch(b)) return rc;
+    if (int rc = validate_hist(b, K, hist, hist_offsets)) return rc;
+    cudaSetDevice(c->device);
+    Plan pl;
+    if (int rc = make_plan(c, b, nullptr, 0, K, pl)) return rc;
+    if (int rc = ensure_line_bufs(c, pl.S, K)) return rc;
+    if (int rc = upload_plan(c, pl, nullptr, 0, hist ? hist_offsets : nullptr)) return rc;
+    mark(c, 0);
+    if (int rc = launched(c, launch_check_finite(b->y, pl.total, P<int>(c->status), c->stream)))
+        return rc;
+    for (int i = 1; i <= 4; ++i) mark(c, i);
+    rqa_line_outputs lo{hist, hist_offsets, lmax, count, stencil};
+    LineBufs lb;
+    if (int rc = lines_and_outputs(c, pl, eps, &lo, lb)) return rc;
+    if (int rc = line_outputs_tail(c, pl, &lo, lb)) return rc;
+    mark(c, 6);
+    return RQA_OK;
+}
+
+int rqa_set_timing(rqa_ctx *c, int enable)
+{
+    if (!c) return RQA_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    if (enable && !c->ev[0]) {
+        for (int i = 0; i < 7; ++i)
+            if (cudaEventCreate(&c->ev[i]) != cudaSuccess) return check_cuda(cudaGetLastError());
+    }
+    c->timing = enable != 0;
+    c->ev_recorded = false;
+    return RQA_OK;
+}
+
+int rqa_phase_times(rqa_ctx *c, float *ms, int n)
+{
+    if (!c || !ms || n < 6) return RQA_ERR_INVALID_ARG;
+    for (int i = 0; i < 6; ++i) ms[i] = 0.f;
+    if (!c->timing || !c->ev_recorded) return RQA_OK;
+    cudaSetDevice(c->device);
+    if (cudaEventSynchronize(c->ev[6]) != cudaSuccess) return check_cuda(cudaGetLastError());
+    for (int i = 0; i < 6; ++i)
+        if (cudaEventElapsedTime(&ms[i], c->ev[i], c->ev[i + 1]) != cudaSuccess)
+            return check_cuda(cudaGetLastError());
+    return RQA_OK;
+}
+
+uint64_t rqa_kernel_launches(rqa_ctx *c) { return c ? c->launches : 0; }
+
+}  // extern "C"

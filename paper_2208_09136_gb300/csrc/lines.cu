@@ -1,0 +1,286 @@
+// Diagonal lines of the never-materialised recurrence matrices for all K
+// thresholds at once (Eq. 4; Sect. 4: upper triangle, cells computed on the
+// fly, line lengths from the beginnings and ends of runs).
+//
+// A warp owns a band of D consecutive diagonals and walks down it 32 rows at
+// a time.  For each diagonal of the band, lane t computes the distance of
+// cell (i0+t, i0+t+delta) and its rank r = #{k : eps_k < d} (a 5-step
+// branch-free search over the sorted thresholds, padded to 32).  Five
+// __ballot_sync calls publish the bit planes of r to the warp; lane k then
+// rebuilds its own 32-cell recurrence word {t : r_t <= k} with a bit-sliced
+// comparison, and reads its runs with __ffs/__clz/popc bit tricks.  The run
+// still open at bit 31 is carried (per diagonal, in a register) into the next
+// 32 rows.  So all K thresholds share one distance evaluation per cell, and
+// the bitmask work per cell is spread over K lanes.
+//
+// Outputs per (series, threshold): C_k = recurrent cells (popc of the words),
+// P_k(l) for l <= LSH in shared memory (flushed once per work item), longer
+// lines straight to the caller's full histogram, and L_max.
+#include <cstdint>
+#include "rqa_common.cuh"
+
+namespace rqa {
+
+constexpr int HS_STRIDE = LSH + 1;  // +1: spreads lanes of one length over banks
+
+int lines_smem_bytes(int K) { return K * HS_STRIDE * 4; }
+
+template <bool HIST>
+struct LineSink {
+    uint32_t *hs;           // shared [K][HS_STRIDE], index = length
+    uint64_t *hist;         // this series' full histogram row for lane k, or null
+    uint32_t lmax;
+    __device__ __forceinline__ void emit(uint32_t len)
+    {
+        if (len <= (uint32_t)LSH) {
+            atomicAdd(hs + len, 1u);
+        } else if (HIST) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(hist + (len - 1)), 1ull);
+        }
+        lmax = max(lmax, len);
+    }
+};
+
+// Runs of one 32-cell word (bit t = row i0+t) joined with the open run c.
+template <class Sink>
+__device__ __forceinline__ void runs_word(uint32_t w, uint32_t &c, Sink &sink)
+{
+    if (w == 0u) {
+        if (c) {
+            sink.emit(c);
+            c = 0;
+        }
+        return;
+    }
+    if (w == FULL) {
+        c += 32;
+        return;
+    }
+    const uint32_t t0 = __ffs(~w) - 1;   // ones at the bottom: they extend the open run
+    const uint32_t lead = c + t0;
+    if (lead) sink.emit(lead);           // ... which ends below the first zero
+    const uint32_t tl = __clz(~w);       // ones at the top: they stay open
+    uint32_t mid = w & (FULL << t0);
+    if (tl) mid &= (FULL >> tl);
+    while (mid) {                        // closed runs strictly inside the word
+        const uint32_t low = mid & (0u - mid);
+        const uint32_t nxt = mid + low;  // clears the lowest run
+        sink.emit(__popc(mid & ~nxt));
+        mid &= nxt;
+    }
+    c = tl;
+}
+
+template <int D, int M, bool HIST>
+__global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int K)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t *hs = reinterpret_cast<uint32_t *>(smem);
+    __shared__ uint32_t epsb[32];
+    __shared__ int slot;
+    __shared__ int bad;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool klane = lane < K;
+
+    // lane k's bits as masks, for the bit-sliced test r <= k
+    uint32_t km[5];
+#pragma unroll
+    for (int b = 0; b < 5; ++b) km[b] = ((lane >> b) & 1) ? FULL : 0u;
+
+    for (int x = threadIdx.x; x < K * HS_STRIDE; x += THREADS) hs[x] = 0;
+
+    for (;;) {
+        const int it = next_item(a.queue, a.n_items, &slot);
+        if (it < 0) break;
+        const Item item = a.items[it];
+        const SeriesDev sd = a.series[item.s];
+        if (warp == 0) {
+            uint32_t v = 0xffffffffu;   // padding: above every key
+            bool ok = true;
+            if (klane) {
+                v = __float_as_uint(lb.eps[(int64_t)item.s * K + lane]);
+                if (v == 0x80000000u) v = 0u;                        // -0 == +0
+                if ((v & 0x80000000u) || v > 0x7f800000u) ok = false;  // negative or NaN
+            }
+            const uint32_t prev = __shfl_up_sync(FULL, v, 1);
+            if (klane && lane > 0 && prev > v) ok = false;           // not ascending
+            const bool all_ok = __all_sync(FULL, ok);
+            epsb[lane] = v;
+            if (lane == 0) {
+                bad = !all_ok;
+                if (!all_ok) set_status(a.status, 8 /*UNSORTED*/);
+            }
+        }
+        __syncthreads();
+        if (bad) continue;
+
+        const float *ys = a.y + sd.off;
+        uint64_t cnt = 0;
+        LineSink<HIST> sink;
+        sink.hs = hs + lane * HS_STRIDE;
+        sink.hist = nullptr;
+        if (HIST && klane)
+            sink.hist = lb.hist + lb.hist_off[item.s] + (int64_t)lane * (sd.ne - 1);
+        sink.lmax = 0;
+
+        for (int b = item.b_lo + warp; b < item.b_hi; b += WARPS) {
+            int d_lo, d_hi;
+            band_range(b, a.band, sd.ne, d_lo, d_hi);
+            const int rows = sd.ne - d_lo;
+            uint32_t carry[D];
+#pragma unroll
+            for (int j = 0; j < D; ++j) carry[j] = 0;
+            for (int i0 = 0; i0 < rows; i0 += 32) {
+                const int i = i0 + lane;
+                RowVec<M> rv;
+                if (i < rows) rv.load(ys, i, sd.tau, sd.m);
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    const int dl = d_lo + j;
+                    uint32_t r = 31;  // outside the diagonal: recurrent for no k
+                    if (i < sd.ne - dl) {
+                        const uint32_t key =
+                            __float_as_uint(rv.dist(ys, i, i + dl, sd.tau, sd.m));
+                        r = 0;
+                        r += (epsb[r + 15] < key) ? 16u : 0u;
+                        r += (epsb[r + 7] < key) ? 8u : 0u;
+                        r += (epsb[r + 3] < key) ? 4u : 0u;
+                        r += (epsb[r + 1] < key) ? 2u : 0u;
+                        r += (epsb[r] < key) ? 1u : 0u;
+                    }
+                    const uint32_t B0 = __ballot_sync(FULL, r & 1u);
+                    const uint32_t B1 = __ballot_sync(FULL, r & 2u);
+                    const uint32_t B2 = __ballot_sync(FULL, r & 4u);
+                    const uint32_t B3 = __ballot_sync(FULL, r & 8u);
+                    const uint32_t B4 = __ballot_sync(FULL, r & 16u);
+                    if (klane) {
+                        // gt = {t : r_t > k}, most significant bit plane first
+                        uint32_t gt = B4 & ~km[4];
+                        uint32_t eq = ~(B4 ^ km[4]);
+                        gt |= eq & B3 & ~km[3];
+                        eq &= ~(B3 ^ km[3]);
+                        gt |= eq & B2 & ~km[2];
+                        eq &= ~(B2 ^ km[2]);
+                        gt |= eq & B1 & ~km[1];
+                        eq &= ~(B1 ^ km[1]);
+                        gt |= eq & B0 & ~km[0];
+                        const uint32_t w = ~gt;
+                        cnt += __popc(w);
+                        runs_word(w, carry[j], sink);
+                    }
+                }
+            }
+            if (klane) {
+#pragma unroll
+                for (int j = 0; j < D; ++j)
+                    if (carry[j]) sink.emit(carry[j]);
+            }
+        }
+        if (klane) {
+            const int64_t o = (int64_t)item.s * K + lane;
+            if (cnt) atomicAdd(reinterpret_cast<unsigned long long *>(lb.count + o),
+                               (unsigned long long)cnt);
+            if (sink.lmax) atomicMax(lb.lmax + o, sink.lmax);
+        }
+        __syncthreads();
+        uint64_t *gs = lb.hshort + (int64_t)item.s * K * LSH;
+        for (int x = threadIdx.x; x < K * LSH; x += THREADS) {
+            const int k = x / LSH, l = x - k * LSH + 1;
+            const uint32_t v = hs[k * HS_STRIDE + l];
+            if (v) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(gs + x), (unsigned long long)v);
+                hs[k * HS_STRIDE + l] = 0;
+            }
+        }
+    }
+}
+
+template <int D, bool HIST>
+static cudaError_t launch_lines_dm(const CellArgs &a, const LineBufs &lb, int K, int grid,
+                                   int max_m, cudaStream_t st)
+{
+    void (*kern)(CellArgs, LineBufs, int);
+    switch (max_m) {
+    case 1: kern = k_lines<D, 1, HIST>; break;
+    case 2: kern = k_lines<D, 2, HIST>; break;
+    case 3: kern = k_lines<D, 3, HIST>; break;
+    case 4: kern = k_lines<D, 4, HIST>; break;
+    default: kern = k_lines<D, 0, HIST>; break;
+    }
+    const int smem = lines_smem_bytes(K);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, THREADS, smem, st>>>(a, lb, K);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lines(const CellArgs &a, const LineBufs &lb, int K, int grid, int max_m,
+                         cudaStream_t st)
+{
+    const bool hist = lb.hist != nullptr;
+    if (a.band != 16) return cudaErrorInvalidValue;
+    return hist ? launch_lines_dm<16, true>(a, lb, K, grid, max_m, st)
+                : launch_lines_dm<16, false>(a, lb, K, grid, max_m, st);
+}
+
+// DET_k(lmin) = (C_k - sum_{l < lmin} l P_k(l)) / C_k  (Eq. 4), an FP64 ratio of
+// exact integers, and the average over k in order (Eq. avgDET).
+__global__ void k_finalize_det(LineBufs lb, int K, const int32_t *lmin, int n_lmin, double *det,
+                               double *det_avg)
+{
+    __shared__ double dk[KMAX * LMIN_MAX];
+    const int s = blockIdx.x;
+    const int t = threadIdx.x;
+    if (t < K) {
+        const int64_t o = (int64_t)s * K + t;
+        const uint64_t C = lb.count[o];
+        const uint64_t *h = lb.hshort + o * LSH;
+        for (int j = 0; j < n_lmin; ++j) {
+            uint64_t shortmass = 0;
+            for (int l = 1; l < lmin[j]; ++l) shortmass += (uint64_t)l * h[l - 1];
+            const double v = (double)(C - shortmass) / (double)C;
+            dk[t * LMIN_MAX + j] = v;
+            if (det) det[o * n_lmin + j] = v;
+        }
+    }
+    __syncthreads();
+    if (t < n_lmin) {
+        double acc = 0.0;
+        for (int k = 0; k < K; ++k) acc = acc + dk[k * LMIN_MAX + t];
+        det_avg[(int64_t)s * n_lmin + t] = acc / (double)K;
+    }
+}
+
+cudaError_t launch_finalize_det(const LineBufs &lb, const SeriesDev *, int S, int K,
+                                const int32_t *lmin_dev, int n_lmin, double *det,
+                                double *det_avg, cudaStream_t st)
+{
+    k_finalize_det<<<S, 32, 0, st>>>(lb, K, lmin_dev, n_lmin, det, det_avg);
+    return cudaGetLastError();
+}
+
+// Short lengths into the caller's full histogram; stencil count C_k - P_k(1).
+__global__ void k_finalize_hist(LineBufs lb, const SeriesDev *series, int K, uint64_t *stencil)
+{
+    const int s = blockIdx.x;
+    const int ne = series[s].ne;
+    const int nl = min(LSH, ne - 1);
+    for (int x = threadIdx.x; x < K * LSH; x += blockDim.x) {
+        const int k = x / LSH, l = x - k * LSH + 1;
+        const uint64_t v = lb.hshort[((int64_t)s * K + k) * LSH + (l - 1)];
+        if (lb.hist && l <= nl) lb.hist[lb.hist_off[s] + (int64_t)k * (ne - 1) + (l - 1)] = v;
+    }
+    if (stencil && threadIdx.x < K) {
+        const int64_t o = (int64_t)s * K + threadIdx.x;
+        stencil[o] = lb.count[o] - lb.hshort[o * LSH];
+    }
+}
+
+cudaError_t launch_finalize_hist(const LineBufs &lb, const SeriesDev *series, int S, int K,
+                                 uint64_t *stencil, cudaStream_t st)
+{
+    k_finalize_hist<<<S, 256, 0, st>>>(lb, series, K, stencil);
+    return cudaGetLastError();
+}
+
+}  // namespace rqa

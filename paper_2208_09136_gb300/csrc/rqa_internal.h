@@ -1,0 +1,98 @@
+// Internal declarations shared by the host API and the kernels of librqa.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rqa {
+
+// FP32 distances are non-negative, so their bit patterns ("keys") order like
+// the values and use only bits 30..0.  Exact selection splits a key into an
+// 11-bit coarse digit (bits 30..20), a 10-bit middle digit (19..10) and a
+// 10-bit low digit (9..0).
+constexpr int KMAX = 31;
+constexpr int COARSE_SHIFT = 20;
+constexpr int NCOARSE = 1 << 11;   // 2048 coarse buckets
+constexpr int NFINE = 1 << 10;     // 1024 bins per middle / low digit group
+constexpr int NSUB_MAX = 24;       // bracket-subdivided coarse buckets per series
+constexpr int LSH = 128;           // line lengths 1..LSH counted in shared memory
+constexpr int LMIN_MAX = 8;        // entries of an lmin list
+constexpr int THREADS = 256;       // threads per CTA of the cell kernels
+constexpr int WARPS = THREADS / 32;
+
+// Counting rounds of the selection.
+enum Round : int {
+    R_COARSE = 0,      // coarse digit of every key
+    R_COARSE_SUB = 1,  // coarse digit, bracket buckets already split by middle digit
+    R_MID = 2,         // middle digit of keys whose coarse digit holds a target
+    R_FINAL = 3        // low digit of keys whose 21-bit prefix holds a target
+};
+
+struct SeriesDev {
+    int64_t off;      // first value of the series in the batch buffer
+    int32_t n;        // N
+    int32_t ne;       // Ne = N - (m-1) tau
+    int32_t m, tau;
+    uint64_t P;       // Ne (Ne - 1) / 2
+    int32_t nbands;   // ceil((Ne - 1) / band)
+    int32_t pad;
+};
+
+struct Item {         // bands [b_lo, b_hi) of series s: one CTA's unit of work
+    int32_t s, b_lo, b_hi, pad;
+};
+
+// Device buffers of the selection state; [s*K + k] unless stated.
+struct SelBufs {
+    const uint64_t *T;     // target counts
+    uint32_t *prefix;      // key bits fixed so far
+    uint8_t *level;        // 1: coarse digit known, 2: 21-bit prefix known
+    uint64_t *rank;        // rank of the target within its current key interval
+    uint64_t *below;       // keys below the current key interval
+    int8_t *tab_sub;       // [s][NCOARSE] bracket split buckets -> group, -1
+    int8_t *tab_mid;       // [s][NCOARSE] coarse bucket -> middle group, -1
+    int8_t *tab_fin1;      // [s][NCOARSE] coarse bucket -> final super group, -1
+    int8_t *tab_fin2;      // [s][KMAX][NFINE] (super group, middle digit) -> group
+    int32_t *n_sub, *n_mid, *n_fin;   // [s]
+    uint64_t *hist;        // [s][hstride]: NCOARSE coarse bins then fine bins
+    int64_t hstride;
+};
+
+struct CellArgs {
+    const float *y;
+    const SeriesDev *series;
+    const Item *items;
+    int32_t n_items;
+    int32_t band;
+    unsigned int *queue;   // persistent-CTA ticket counter, zeroed before launch
+    int *status;
+};
+
+// Kernels (launch wrappers return cudaGetLastError()).
+cudaError_t launch_check_finite(const float *y, int64_t n, int *status, cudaStream_t st);
+cudaError_t launch_count(int round, const CellArgs &a, const SelBufs &sb, int K, int grid,
+                         int max_m, cudaStream_t st);
+cudaError_t launch_select(int round, const SelBufs &sb, const SeriesDev *series, int s_begin,
+                          int n_series, int K, float *eps_out, uint64_t *le_out,
+                          uint64_t *lt_out, int *status, cudaStream_t st);
+
+struct LineBufs {
+    const float *eps;      // [s*K + k], ascending per series
+    uint64_t *count;       // [s*K + k]
+    uint32_t *lmax;        // [s*K + k]
+    uint64_t *hshort;      // [s][K][LSH]: P_k(l) for l = 1..LSH
+    uint64_t *hist;        // caller's full histogram or nullptr
+    const int64_t *hist_off;  // device [S+1] offsets into hist (nullptr if no hist)
+};
+cudaError_t launch_lines(const CellArgs &a, const LineBufs &lb, int K, int grid, int max_m,
+                         cudaStream_t st);
+cudaError_t launch_finalize_det(const LineBufs &lb, const SeriesDev *series, int S, int K,
+                                const int32_t *lmin_dev, int n_lmin, double *det,
+                                double *det_avg, cudaStream_t st);
+cudaError_t launch_finalize_hist(const LineBufs &lb, const SeriesDev *series, int S, int K,
+                                 uint64_t *stencil, cudaStream_t st);
+
+// Largest dynamic shared memory a count round needs for K thresholds.
+int count_smem_bytes(int round, int K);
+int lines_smem_bytes(int K);
+
+}  // namespace rqa

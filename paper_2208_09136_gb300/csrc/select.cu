@@ -1,0 +1,462 @@
+// Exact selection of the RR-preselected thresholds (Sect. 2, "preselect RR
+// and use the corresponding value for eps"; Eq. 3).
+//
+// eps_k is the T_k-th smallest upper-triangle distance.  Distances are never
+// stored: every counting round recomputes them over diagonal bands and
+// histograms one digit of their FP32 bit pattern (the "key"; non-negative
+// floats order like their bit patterns).  Rounds:
+//   R_COARSE      bits 30..20 of every key                    -> 2048 bins
+//   R_COARSE_SUB  as R_COARSE, but coarse buckets a learned bracket marks are
+//                 split at once by bits 19..10 (skips R_MID for those targets)
+//   R_MID         bits 19..10 of keys in a target's coarse bucket
+//   R_FINAL       bits 9..0 of keys in a target's 21-bit prefix
+// After each round a select kernel turns the histogram into (prefix, rank,
+// below) per target.  After R_FINAL the key is complete: eps_k, and
+// #{d < eps_k} = below, #{d <= eps_k} = below + (keys equal to eps_k).
+#include <cstdint>
+#include "rqa_common.cuh"
+
+namespace rqa {
+
+// ------------------------------------------------------------ finiteness
+__global__ void k_check_finite(const float *__restrict__ y, int64_t n, int *status)
+{
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(y[i]);
+    if (__any_sync(FULL, bad) && (threadIdx.x & 31) == 0) set_status(status, 3 /*NONFINITE*/);
+}
+
+cudaError_t launch_check_finite(const float *y, int64_t n, int *status, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_check_finite<<<(int)blocks, 256, 0, st>>>(y, n, status);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ counting
+int count_smem_bytes(int round, int K)
+{
+    switch (round) {
+    case R_COARSE: return NCOARSE * 4;
+    case R_COARSE_SUB: return (NCOARSE + NSUB_MAX * NFINE) * 4 + NCOARSE;
+    case R_MID: return K * NFINE * 4 + NCOARSE;
+    default: return K * NFINE * 4 + NCOARSE + K * NFINE;
+    }
+}
+
+template <int ROUND>
+__device__ __forceinline__ int bin_of(uint32_t key, const int8_t *t1, const int8_t *t2)
+{
+    if (ROUND == R_COARSE) return (int)(key >> COARSE_SHIFT);
+    if (ROUND == R_COARSE_SUB) {
+        int c = (int)(key >> COARSE_SHIFT);
+        int g = t1[c];
+        return g < 0 ? c : NCOARSE + g * NFINE + (int)((key >> 10) & (NFINE - 1));
+    }
+    if (ROUND == R_MID) {
+        int g = t1[key >> COARSE_SHIFT];
+        return g < 0 ? -1 : g * NFINE + (int)((key >> 10) & (NFINE - 1));
+    }
+    int g1 = t1[key >> COARSE_SHIFT];
+    if (g1 < 0) return -1;
+    int g = t2[g1 * NFINE + (int)((key >> 10) & (NFINE - 1))];
+    return g < 0 ? -1 : g * NFINE + (int)(key & (NFINE - 1));
+}
+
+// One persistent launch over the work items; each CTA histograms the keys of
+// its item's bands in shared memory and adds the non-zero bins to the
+// series' 64-bit global histogram at the end of the item.
+template <int ROUND, int M>
+__global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int slot;
+    __shared__ int nb_used_sh;
+    const int nbins_max = (ROUND == R_COARSE) ? NCOARSE
+                        : (ROUND == R_COARSE_SUB) ? NCOARSE + NSUB_MAX * NFINE
+                                                  : K * NFINE;
+    uint32_t *h = reinterpret_cast<uint32_t *>(smem);
+    int8_t *t1 = reinterpret_cast<int8_t *>(h + nbins_max);
+    int8_t *t2 = t1 + NCOARSE;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    for (int x = threadIdx.x; x < nbins_max; x += THREADS) h[x] = 0;
+
+    for (;;) {
+        const int it = next_item(a.queue, a.n_items, &slot);
+        if (it < 0) break;
+        const Item item = a.items[it];
+        const SeriesDev sd = a.series[item.s];
+        if (threadIdx.x == 0) {
+            int nb;
+            if (ROUND == R_COARSE) nb = NCOARSE;
+            else if (ROUND == R_COARSE_SUB) nb = NCOARSE + sb.n_sub[item.s] * NFINE;
+            else if (ROUND == R_MID) nb = sb.n_mid[item.s] * NFINE;
+            else nb = sb.n_fin[item.s] * NFINE;
+            nb_used_sh = nb;
+        }
+        if (ROUND != R_COARSE) {
+            const int8_t *src = (ROUND == R_COARSE_SUB) ? sb.tab_sub
+                              : (ROUND == R_MID) ? sb.tab_mid : sb.tab_fin1;
+            src += (int64_t)item.s * NCOARSE;
+            for (int x = threadIdx.x; x < NCOARSE; x += THREADS) t1[x] = src[x];
+            if (ROUND == R_FINAL) {
+                const int8_t *s2 = sb.tab_fin2 + (int64_t)item.s * KMAX * NFINE;
+                for (int x = threadIdx.x; x < K * NFINE; x += THREADS) t2[x] = s2[x];
+            }
+        }
+        __syncthreads();
+        const int nb_used = nb_used_sh;
+        if (nb_used == 0) continue;  // no target of this series needs this round
+
+        const float *ys = a.y + sd.off;
+        for (int b = item.b_lo + warp; b < item.b_hi; b += WARPS) {
+            int d_lo, d_hi;
+            band_range(b, a.band, sd.ne, d_lo, d_hi);
+            const int rows = sd.ne - d_lo;
+            int last = -1;
+            uint32_t run = 0;
+            for (int i0 = 0; i0 < rows; i0 += 32) {
+                const int i = i0 + lane;
+                RowVec<M> rv;
+                if (i < rows) rv.load(ys, i, sd.tau, sd.m);
+                for (int dl = d_lo; dl < d_hi; ++dl) {
+                    if (i < sd.ne - dl) {
+                        const uint32_t key = __float_as_uint(rv.dist(ys, i, i + dl, sd.tau, sd.m));
+                        const int bin = bin_of<ROUND>(key, t1, t2);
+                        if (bin >= 0) {
+                            // consecutive cells of a lane are neighbours in the
+                            // matrix: aggregate equal bins before the atomic
+                            if (bin == last) {
+                                ++run;
+                            } else {
+                                if (run) atomicAdd(&h[last], run);
+                                last = bin;
+                                run = 1;
+                            }
+                        }
+                    }
+                }
+            }
+            if (run) atomicAdd(&h[last], run);
+        }
+        __syncthreads();
+        uint64_t *gh = sb.hist + (int64_t)item.s * sb.hstride + (ROUND >= R_MID ? NCOARSE : 0);
+        for (int x = threadIdx.x; x < nb_used; x += THREADS) {
+            const uint32_t v = h[x];
+            if (v) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(gh + x), (unsigned long long)v);
+                h[x] = 0;
+            }
+        }
+    }
+}
+
+template <int ROUND>
+static cudaError_t launch_count_m(const CellArgs &a, const SelBufs &sb, int K, int grid,
+                                  int max_m, cudaStream_t st)
+{
+    const int smem = count_smem_bytes(ROUND, K);
+    void (*kern)(CellArgs, SelBufs, int);
+    switch (max_m) {
+    case 1: kern = k_count<ROUND, 1>; break;
+    case 2: kern = k_count<ROUND, 2>; break;
+    case 3: kern = k_count<ROUND, 3>; break;
+    case 4: kern = k_count<ROUND, 4>; break;
+    default: kern = k_count<ROUND, 0>; break;
+    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, THREADS, smem, st>>>(a, sb, K);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count(int round, const CellArgs &a, const SelBufs &sb, int K, int grid,
+                         int max_m, cudaStream_t st)
+{
+    switch (round) {
+    case R_COARSE: return launch_count_m<R_COARSE>(a, sb, K, grid, max_m, st);
+    case R_COARSE_SUB: return launch_count_m<R_COARSE_SUB>(a, sb, K, grid, max_m, st);
+    case R_MID: return launch_count_m<R_MID>(a, sb, K, grid, max_m, st);
+    default: return launch_count_m<R_FINAL>(a, sb, K, grid, max_m, st);
+    }
+}
+
+// ------------------------------------------------------------ selection
+// In-place inclusive scan of n 64-bit values in shared memory (n a multiple
+// of THREADS).
+__device__ void block_scan_u64(uint64_t *v, int n, uint64_t *warp_tot)
+{
+    const int per = n / THREADS;
+    const int t = threadIdx.x;
+    uint64_t s = 0;
+    for (int x = 0; x < per; ++x) {
+        s += v[t * per + x];
+        v[t * per + x] = s;
+    }
+    uint64_t incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t u = __shfl_up_sync(FULL, incl, o);
+        if ((t & 31) >= o) incl += u;
+    }
+    if ((t & 31) == 31) warp_tot[t >> 5] = incl;
+    __syncthreads();
+    uint64_t wpre = 0;
+    for (int w = 0; w < (t >> 5); ++w) wpre += warp_tot[w];
+    const uint64_t excl = wpre + incl - s;
+    for (int x = 0; x < per; ++x) v[t * per + x] += excl;
+    __syncthreads();
+}
+
+// Smallest index x with a[x] >= v (n if none).
+__device__ __forceinline__ int lower_bound_u64(const uint64_t *a, int n, uint64_t v)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Load the NFINE bins of fine group g of series s and scan them.
+__device__ void load_scan_group(const uint64_t *gh_fine, int g, uint64_t *cum, uint64_t *wt)
+{
+    const uint64_t *src = gh_fine + (int64_t)g * NFINE;
+    for (int x = threadIdx.x; x < NFINE; x += THREADS) cum[x] = src[x];
+    __syncthreads();
+    block_scan_u64(cum, NFINE, wt);
+}
+
+// One CTA per series.  ROUND is the counting round whose histogram is read.
+template <int ROUND>
+__global__ void __launch_bounds__(THREADS)
+k_select(SelBufs sb, const SeriesDev *series, int s_begin, int K, float *eps_out,
+         uint64_t *le_out, uint64_t *lt_out, int *status)
+{
+    __shared__ uint64_t cum[NCOARSE];
+    __shared__ uint64_t wt[WARPS];
+    __shared__ uint32_t pre[KMAX];
+    __shared__ uint8_t lev[KMAX];
+    __shared__ uint64_t rnk[KMAX], blw[KMAX];
+    __shared__ int grp[KMAX];
+    __shared__ int ngroups;
+    const int s = s_begin + blockIdx.x;
+    const int t = threadIdx.x;
+    const int64_t sk = (int64_t)s * K;
+    const uint64_t *gh = sb.hist + (int64_t)s * sb.hstride;
+    const uint64_t *gfine = gh + NCOARSE;
+    (void)series;
+
+    if (ROUND == R_COARSE || ROUND == R_COARSE_SUB) {
+        // bucket totals; a split bucket's keys sit in its fine group
+        for (int x = t; x < NCOARSE; x += THREADS) cum[x] = gh[x];
+        __syncthreads();
+        if (ROUND == R_COARSE_SUB) {
+            __shared__ int inv[NSUB_MAX];
+            const int nsub = sb.n_sub[s];
+            const int8_t *tab = sb.tab_sub + (int64_t)s * NCOARSE;
+            if (t < NSUB_MAX) inv[t] = -1;
+            __syncthreads();
+            for (int c = t; c < NCOARSE; c += THREADS) {
+                const int g = tab[c];
+                if (g >= 0 && g < NSUB_MAX) inv[g] = c;
+            }
+            __syncthreads();
+            for (int g = 0; g < nsub; ++g) {
+                uint64_t part = 0;
+                for (int x = t; x < NFINE; x += THREADS) part += gfine[(int64_t)g * NFINE + x];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+                if ((t & 31) == 0) wt[t >> 5] = part;
+                __syncthreads();
+                if (t == 0 && inv[g] >= 0) {
+                    uint64_t tot = 0;
+                    for (int w = 0; w < WARPS; ++w) tot += wt[w];
+                    cum[inv[g]] += tot;
+                }
+                __syncthreads();
+            }
+        }
+        block_scan_u64(cum, NCOARSE, wt);
+        if (t < K) {
+            const uint64_t R = sb.T[sk + t];
+            const int c = lower_bound_u64(cum, NCOARSE, R);
+            if (c >= NCOARSE || R == 0) {
+                set_status(status, 10 /*INTERNAL*/);
+                pre[t] = 0; lev[t] = 1; rnk[t] = 1; blw[t] = 0;
+            } else {
+                const uint64_t below = c ? cum[c - 1] : 0;
+                pre[t] = (uint32_t)c;
+                lev[t] = 1;
+                rnk[t] = R - below;
+                blw[t] = below;
+            }
+            grp[t] = -1;
+        }
+        __syncthreads();
+        if (ROUND == R_COARSE_SUB) {
+            const int8_t *tab = sb.tab_sub + (int64_t)s * NCOARSE;
+            if (t < K) grp[t] = tab[pre[t]];
+            __syncthreads();
+            const int nsub = sb.n_sub[s];
+            for (int g = 0; g < nsub; ++g) {
+                bool any = false;
+                for (int k = 0; k < K; ++k) any |= (grp[k] == g);
+                if (!any) continue;
+                load_scan_group(gfine, g, cum, wt);
+                if (t < K && grp[t] == g) {
+                    const int x = lower_bound_u64(cum, NFINE, rnk[t]);
+                    if (x >= NFINE) {
+                        set_status(status, 10);
+                    } else {
+                        const uint64_t below = x ? cum[x - 1] : 0;
+                        pre[t] = (pre[t] << 10) | (uint32_t)x;
+                        lev[t] = 2;
+                        rnk[t] -= below;
+                        blw[t] += below;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // middle-round table: coarse bucket -> group, for targets at level 1
+        int8_t *tm = sb.tab_mid + (int64_t)s * NCOARSE;
+        for (int x = t; x < NCOARSE; x += THREADS) tm[x] = -1;
+        __syncthreads();
+        if (t == 0) {
+            int g = 0;
+            for (int k = 0; k < K; ++k) {
+                if (lev[k] != 1) continue;
+                if (tm[pre[k]] < 0) tm[pre[k]] = (int8_t)g++;
+            }
+            sb.n_mid[s] = g;
+        }
+        if (t < K) {
+            sb.prefix[sk + t] = pre[t];
+            sb.level[sk + t] = lev[t];
+            sb.rank[sk + t] = rnk[t];
+            sb.below[sk + t] = blw[t];
+        }
+        return;
+    }
+
+    // R_MID and R_FINAL: state from global memory
+    if (t < K) {
+        pre[t] = sb.prefix[sk + t];
+        lev[t] = sb.level[sk + t];
+        rnk[t] = sb.rank[sk + t];
+        blw[t] = sb.below[sk + t];
+    }
+    __syncthreads();
+
+    if (ROUND == R_MID) {
+        const int8_t *tm = sb.tab_mid + (int64_t)s * NCOARSE;
+        if (t < K) grp[t] = (lev[t] == 1) ? tm[pre[t]] : -1;
+        __syncthreads();
+        const int nmid = sb.n_mid[s];
+        for (int g = 0; g < nmid; ++g) {
+            load_scan_group(gfine, g, cum, wt);
+            if (t < K && grp[t] == g) {
+                const int x = lower_bound_u64(cum, NFINE, rnk[t]);
+                if (x >= NFINE) {
+                    set_status(status, 10);
+                } else {
+                    const uint64_t below = x ? cum[x - 1] : 0;
+                    pre[t] = (pre[t] << 10) | (uint32_t)x;
+                    lev[t] = 2;
+                    rnk[t] -= below;
+                    blw[t] += below;
+                }
+            }
+            __syncthreads();
+        }
+        // final-round tables for all targets (every target is at level 2 now)
+        int8_t *f1 = sb.tab_fin1 + (int64_t)s * NCOARSE;
+        int8_t *f2 = sb.tab_fin2 + (int64_t)s * KMAX * NFINE;
+        for (int x = t; x < NCOARSE; x += THREADS) f1[x] = -1;
+        for (int x = t; x < K * NFINE; x += THREADS) f2[x] = -1;
+        __syncthreads();
+        if (t == 0) {
+            int g1 = 0, g = 0;
+            for (int k = 0; k < K; ++k) {
+                const uint32_t c = pre[k] >> 10, mid = pre[k] & (NFINE - 1);
+                if (f1[c] < 0) f1[c] = (int8_t)g1++;
+                int8_t *e = f2 + f1[c] * NFINE + mid;
+                if (*e < 0) *e = (int8_t)g++;
+            }
+            sb.n_fin[s] = g;
+        }
+        if (t < K) {
+            sb.prefix[sk + t] = pre[t];
+            sb.level[sk + t] = lev[t];
+            sb.rank[sk + t] = rnk[t];
+            sb.below[sk + t] = blw[t];
+        }
+        return;
+    }
+
+    // R_FINAL: the low digit completes the key
+    {
+        const int8_t *f1 = sb.tab_fin1 + (int64_t)s * NCOARSE;
+        const int8_t *f2 = sb.tab_fin2 + (int64_t)s * KMAX * NFINE;
+        if (t < K) {
+            const int g1 = f1[pre[t] >> 10];
+            grp[t] = (g1 < 0) ? -1 : f2[g1 * NFINE + (pre[t] & (NFINE - 1))];
+            if (grp[t] < 0) set_status(status, 10);
+        }
+        __syncthreads();
+        const int nfin = sb.n_fin[s];
+        for (int g = 0; g < nfin; ++g) {
+            load_scan_group(gfine, g, cum, wt);
+            if (t < K && grp[t] == g) {
+                const int x = lower_bound_u64(cum, NFINE, rnk[t]);
+                if (x >= NFINE) {
+                    set_status(status, 10);
+                } else {
+                    const uint64_t lt = blw[t] + (x ? cum[x - 1] : 0);
+                    const uint64_t le = blw[t] + cum[x];
+                    const uint32_t key = (pre[t] << 10) | (uint32_t)x;
+                    eps_out[sk + t] = __uint_as_float(key);
+                    if (le_out) le_out[sk + t] = le;
+                    if (lt_out) lt_out[sk + t] = lt;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+cudaError_t launch_select(int round, const SelBufs &sb, const SeriesDev *series, int s_begin,
+                          int n_series, int K, float *eps_out, uint64_t *le_out,
+                          uint64_t *lt_out, int *status, cudaStream_t st)
+{
+    if (n_series <= 0) return cudaSuccess;
+    switch (round) {
+    case R_COARSE:
+        k_select<R_COARSE><<<n_series, THREADS, 0, st>>>(sb, series, s_begin, K, eps_out, le_out,
+                                                          lt_out, status);
+        break;
+    case R_COARSE_SUB:
+        k_select<R_COARSE_SUB><<<n_series, THREADS, 0, st>>>(sb, series, s_begin, K, eps_out,
+                                                              le_out, lt_out, status);
+        break;
+    case R_MID:
+        k_select<R_MID><<<n_series, THREADS, 0, st>>>(sb, series, s_begin, K, eps_out, le_out,
+                                                       lt_out, status);
+        break;
+    default:
+        k_select<R_FINAL><<<n_series, THREADS, 0, st>>>(sb, series, s_begin, K, eps_out, le_out,
+                                                         lt_out, status);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace rqa

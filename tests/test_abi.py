@@ -1,0 +1,87 @@
+"""CPU-only checks of the C ABI: the library loads, exports every entry point
+that include/rqa.h declares, and its host helpers agree with the oracle.
+No compute call is made without a GPU."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2208_09136_gb300 import build
+    return build.build()
+
+
+def _declared(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rqa_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(built):
+    out = subprocess.run(["nm", "-D", "--defined-only", built], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (rqa_[a-z0-9_]+)", out))
+    headers = [h for h in os.listdir(os.path.join(ROOT, "include")) if h.endswith(".h")]
+    for h in headers:
+        for name in _declared(h):
+            assert name in exported, f"{name} declared in {h} but not exported"
+
+
+def test_binding_resolves_every_symbol(built):
+    import paper_2208_09136_gb300 as rqa
+    L = rqa.lib()
+    for name in _declared("rqa.h"):
+        assert hasattr(L, name)
+    assert rqa.rqa_abi_version() == 1
+
+
+@pytest.mark.parametrize("p", [1, 3, 4753, 49975003, 4999350021, (1 << 61) + 12345])
+def test_target_counts_match_oracle(built, p):
+    import paper_2208_09136_gb300 as rqa
+    from oracle import rqa_oracle as O
+    for rr, den in [(list(range(1, 21)), 100), ([1, 2, 3, 98, 99], 100), ([1, 5], 7)]:
+        got = rqa.rqa_target_counts(p, rr, den)
+        assert np.array_equal(got, O.target_counts(p, rr, den))
+
+
+def test_target_counts_rejects_bad_rates(built):
+    import paper_2208_09136_gb300 as rqa
+    for rr, den in [([0], 100), ([100], 100), ([-1], 100)]:
+        with pytest.raises(rqa.RqaError):
+            rqa.rqa_target_counts(1000, rr, den)
+
+
+def test_error_strings(built):
+    import paper_2208_09136_gb300 as rqa
+    for code in range(0, 11):
+        assert rqa.rqa_error_string(code) != "unknown error"
+    assert rqa.rqa_error_string(99) == "unknown error"
+
+
+def test_create_without_gpu_fails_cleanly(built):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import ctypes
+    from paper_2208_09136_gb300 import abi
+    p = ctypes.c_void_p()
+    cfg = abi._Config(0, None, 0, 0, 0, 0, (ctypes.c_int * 4)())
+    rc = abi.lib().rqa_create(ctypes.byref(p), ctypes.byref(cfg))
+    assert rc == 4 and not p.value  # RQA_ERR_CUDA, no context
+
+
+def test_null_context_is_rejected(built):
+    from paper_2208_09136_gb300 import abi
+    L = abi.lib()
+    assert L.rqa_status(None) == 1
+    assert L.rqa_eps_for_rr(None, None, None, 100, 20, None, None, None) == 1
+    assert L.rqa_det_avg(None, None, None, 100, None, 20, None, 1, None, None, None, None) == 1
+    assert L.rqa_line_hist(None, None, None, 20, None, None, None, None, None) == 1
+    assert L.rqa_set_timing(None, 1) == 1
+    assert L.rqa_kernel_launches(None) == 0
