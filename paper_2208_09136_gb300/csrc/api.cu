@@ -72,6 +72,7 @@ struct rqa_ctx {
 namespace {
 
 struct Plan {
+    const float *y = nullptr;   // the batch's device buffer
     int S = 0, K = 0;
     int mt = 0;                 // common embedding dimension if <= 4, else 0
     int64_t total = 0;          // values in the batch buffer
@@ -168,6 +169,7 @@ int make_plan(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_
               Plan &pl)
 {
     const int S = b->n_series;
+    pl.y = b->y;
     pl.S = S;
     pl.K = K;
     pl.sd.resize(S);
@@ -332,7 +334,8 @@ int run_select(rqa_ctx *c, const Plan &pl, const SelBufs &sb, const Item *items,
 {
     const int K = pl.K;
     const int grid = persistent_grid(c, (size_t)n_items);
-    CellArgs a;
+    CellArgs a{};
+    a.y = pl.y;
     a.series = pl.d_sd;
     a.items = items;
     a.n_items = n_items;
@@ -403,7 +406,8 @@ int run_lines(rqa_ctx *c, const Plan &pl, const float *eps, uint64_t *hist, cons
     if (int rc = check_cuda(cudaMemsetAsync(lb.count, 0, sk * 8, c->stream))) return rc;
     if (int rc = check_cuda(cudaMemsetAsync(lb.lmax, 0, sk * 4, c->stream))) return rc;
     if (int rc = check_cuda(cudaMemsetAsync(lb.hshort, 0, sk * LSH * 8, c->stream))) return rc;
-    CellArgs a;
+    CellArgs a{};
+    a.y = pl.y;
     a.series = pl.d_sd;
     a.band = c->band;
     a.status = P<int>(c->status);

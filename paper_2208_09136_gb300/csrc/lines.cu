@@ -219,6 +219,10 @@ cudaError_t launch_lines(const CellArgs &a, const LineBufs &lb, int K, int grid,
 {
     const bool hist = lb.hist != nullptr;
     if (a.band != 16) return cudaErrorInvalidValue;
+    if (!a.y || !a.series || !a.items || !a.queue || !a.status || !lb.eps || !lb.count ||
+        !lb.lmax || !lb.hshort || (hist && !lb.hist_off) || K < 1 || K > KMAX || grid < 1 ||
+        a.n_items < 1)
+        return cudaErrorInvalidValue;
     return hist ? launch_lines_dm<16, true>(a, lb, K, grid, max_m, st)
                 : launch_lines_dm<16, false>(a, lb, K, grid, max_m, st);
 }

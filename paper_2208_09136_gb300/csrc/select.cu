@@ -99,6 +99,9 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
             else nb = sb.n_fin[item.s] * NFINE;
             nb_used_sh = nb;
         }
+        __syncthreads();
+        const int nb_used = nb_used_sh;
+        if (nb_used == 0) continue;  // no target of this series needs this round
         if (ROUND != R_COARSE) {
             const int8_t *src = (ROUND == R_COARSE_SUB) ? sb.tab_sub
                               : (ROUND == R_MID) ? sb.tab_mid : sb.tab_fin1;
@@ -108,10 +111,8 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
                 const int8_t *s2 = sb.tab_fin2 + (int64_t)item.s * KMAX * NFINE;
                 for (int x = threadIdx.x; x < K * NFINE; x += THREADS) t2[x] = s2[x];
             }
+            __syncthreads();
         }
-        __syncthreads();
-        const int nb_used = nb_used_sh;
-        if (nb_used == 0) continue;  // no target of this series needs this round
 
         const float *ys = a.y + sd.off;
         for (int b = item.b_lo + warp; b < item.b_hi; b += WARPS) {
@@ -178,6 +179,9 @@ static cudaError_t launch_count_m(const CellArgs &a, const SelBufs &sb, int K, i
 cudaError_t launch_count(int round, const CellArgs &a, const SelBufs &sb, int K, int grid,
                          int max_m, cudaStream_t st)
 {
+    if (!a.y || !a.series || !a.items || !a.queue || !a.status || !sb.hist || K < 1 || K > KMAX ||
+        grid < 1 || a.n_items < 1)
+        return cudaErrorInvalidValue;
     switch (round) {
     case R_COARSE: return launch_count_m<R_COARSE>(a, sb, K, grid, max_m, st);
     case R_COARSE_SUB: return launch_count_m<R_COARSE_SUB>(a, sb, K, grid, max_m, st);
