@@ -8,7 +8,7 @@
 #include <vector>
 
 #include "rqa.h"
-#include "rqa_internal.h"
+#include "rqa_common.cuh"
 
 using namespace rqa;
 
@@ -74,18 +74,24 @@ namespace {
 struct Plan {
     const float *y = nullptr;   // the batch's device buffer
     int S = 0, K = 0;
-    int mt = 0;                 // common embedding dimension if <= 4, else 0
+    int mt = 0;                 // Embed code of the batch (distance kernel variant)
     int64_t total = 0;          // values in the batch buffer
     std::vector<SeriesDev> sd;
     std::vector<uint64_t> T;    // S*K (empty if no targets)
     std::vector<Item> items_lpt;             // whole batch, largest first
     std::vector<Item> items_ser;             // grouped by series
     std::vector<int> ser_begin;              // S+1 into items_ser
+    std::vector<int32_t> order;              // series by size, largest first
+    std::vector<int64_t> uprefix;            // S+1 band-count prefix along order
+    std::vector<int32_t> ident;              // 0..S-1
+    std::vector<int64_t> uprefix1;           // [2s], [2s+1] = 0, bands of s
     // device pointers into the arena after upload
     SeriesDev *d_sd = nullptr;
     uint64_t *d_T = nullptr;
     Item *d_lpt = nullptr;
     Item *d_ser = nullptr;
+    int32_t *d_order = nullptr, *d_ident = nullptr;
+    int64_t *d_uprefix = nullptr, *d_uprefix1 = nullptr;
     int32_t *d_lmin = nullptr;
     int64_t *d_hoff = nullptr;
 };
@@ -120,8 +126,8 @@ uint64_t band_cost(int64_t ne, int64_t d_lo, int64_t d_hi)
     return (uint64_t)(n * ne - (d_lo + d_hi - 1) * n / 2);
 }
 
-void build_items(const SeriesDev &s, int sidx, int band, uint64_t target, std::vector<Item> &out,
-                 std::vector<uint64_t> *costs)
+void build_items(const SeriesDev &s, int sidx, int band, uint64_t target, int min_bands,
+                 std::vector<Item> &out, std::vector<uint64_t> *costs)
 {
     Item cur{sidx, 0, 0, 0};
     uint64_t acc = 0;
@@ -130,7 +136,9 @@ void build_items(const SeriesDev &s, int sidx, int band, uint64_t target, std::v
         const int64_t d_hi = std::min<int64_t>(d_lo + band, s.ne);
         acc += band_cost(s.ne, d_lo, d_hi);
         cur.b_hi = b + 1;
-        if (acc >= target || b + 1 == s.nbands) {
+        const bool enough = acc >= target && cur.b_hi - cur.b_lo >= min_bands &&
+                            s.nbands - cur.b_hi >= min_bands;
+        if (enough || acc >= ((uint64_t)1 << 30) || b + 1 == s.nbands) {
             out.push_back(cur);
             if (costs) costs->push_back(acc);
             cur.b_lo = b + 1;
@@ -173,8 +181,8 @@ int make_plan(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_
     pl.S = S;
     pl.K = K;
     pl.sd.resize(S);
-    int m0 = b->m[0];
-    bool uniform = true;
+    int m0 = b->m[0], t0 = b->tau[0];
+    bool uniform = true, uniform_tau = true;
     uint64_t total_cells = 0;
     for (int s = 0; s < S; ++s) {
         SeriesDev &d = pl.sd[s];
@@ -187,38 +195,57 @@ int make_plan(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_
         d.nbands = (d.ne - 1 + c->band - 1) / c->band;
         d.pad = 0;
         uniform &= (d.m == m0);
+        uniform_tau &= (d.tau == t0);
         total_cells += d.P;
     }
     pl.total = b->offsets[S];
-    pl.mt = (uniform && m0 <= 4) ? m0 : 0;
+    pl.mt = E_GENERIC;
+    if (uniform && m0 <= 4) pl.mt = m0;
+    if (uniform && m0 == 1) pl.mt = E_M1T1;  // tau plays no part when m = 1
+    if (uniform && uniform_tau) {
+        if (m0 == 3 && t0 == 1) pl.mt = E_M3T1;
+        if (m0 == 3 && t0 == 3) pl.mt = E_M3T3;
+    }
     if (rr_num) {
         pl.T.resize((size_t)S * K);
         for (int s = 0; s < S; ++s)
             if (rqa_target_counts(pl.sd[s].P, rr_num, rr_den, K, &pl.T[(size_t)s * K]) != RQA_OK)
                 return RQA_ERR_INVALID_ARG;
     }
-    // Work items: runs of consecutive bands of one series.  Batched: sized so
-    // that every SM gets several, then sorted largest first (the persistent
-    // CTAs take them in that order).  Per series: sized from the series alone.
-    const uint64_t workers = (uint64_t)c->sm_count * 4;
+    // CTA work items (counting rounds): runs of consecutive bands of one
+    // series, about three per persistent CTA and at least four bands per warp,
+    // sorted largest first.  Per series: the same rule within the series.
+    const uint64_t ctas = (uint64_t)c->sm_count * 2;
     const uint64_t cap = (uint64_t)1 << 30;  // keeps 32-bit shared counters exact
-    uint64_t tgt = std::max<uint64_t>(total_cells / (workers * 4), (uint64_t)1 << 15);
+    uint64_t tgt = std::max<uint64_t>(total_cells / (ctas * 3), 1);
     tgt = std::min(tgt, cap);
     std::vector<Item> items;
     std::vector<uint64_t> costs;
-    for (int s = 0; s < S; ++s) build_items(pl.sd[s], s, c->band, tgt, items, &costs);
-    std::vector<size_t> order(items.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](size_t x, size_t y) { return costs[x] > costs[y]; });
+    for (int s = 0; s < S; ++s) build_items(pl.sd[s], s, c->band, tgt, 4 * WARPS, items, &costs);
+    std::vector<size_t> idx(items.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) { return costs[x] > costs[y]; });
     pl.items_lpt.resize(items.size());
-    for (size_t i = 0; i < order.size(); ++i) pl.items_lpt[i] = items[order[i]];
+    for (size_t i = 0; i < idx.size(); ++i) pl.items_lpt[i] = items[idx[i]];
     pl.ser_begin.assign(S + 1, 0);
     for (int s = 0; s < S; ++s) {
-        uint64_t t = std::max<uint64_t>(pl.sd[s].P / (workers * 4), (uint64_t)1 << 13);
-        t = std::min(t, cap);
-        build_items(pl.sd[s], s, c->band, t, pl.items_ser, nullptr);
+        uint64_t t = std::min(std::max<uint64_t>(pl.sd[s].P / (ctas * 3), 1), cap);
+        build_items(pl.sd[s], s, c->band, t, 4 * WARPS, pl.items_ser, nullptr);
         pl.ser_begin[s + 1] = (int)pl.items_ser.size();
+    }
+    // warp work units (line pass): every band, series largest first
+    pl.order.resize(S);
+    for (int s = 0; s < S; ++s) pl.order[s] = s;
+    std::stable_sort(pl.order.begin(), pl.order.end(),
+                     [&](int x, int y) { return pl.sd[x].P > pl.sd[y].P; });
+    pl.uprefix.assign(S + 1, 0);
+    for (int i = 0; i < S; ++i) pl.uprefix[i + 1] = pl.uprefix[i] + pl.sd[pl.order[i]].nbands;
+    pl.ident.resize(S);
+    pl.uprefix1.resize(2 * (size_t)S);
+    for (int s = 0; s < S; ++s) {
+        pl.ident[s] = s;
+        pl.uprefix1[2 * s] = 0;
+        pl.uprefix1[2 * s + 1] = pl.sd[s].nbands;
     }
     return RQA_OK;
 }
@@ -230,7 +257,11 @@ int upload_plan(rqa_ctx *c, Plan &pl, const int32_t *lmin, int n_lmin, const int
     const size_t o_T = align16(o_sd + pl.sd.size() * sizeof(SeriesDev));
     const size_t o_lpt = align16(o_T + pl.T.size() * sizeof(uint64_t));
     const size_t o_ser = align16(o_lpt + pl.items_lpt.size() * sizeof(Item));
-    const size_t o_lmin = align16(o_ser + pl.items_ser.size() * sizeof(Item));
+    const size_t o_order = align16(o_ser + pl.items_ser.size() * sizeof(Item));
+    const size_t o_upre = align16(o_order + pl.order.size() * sizeof(int32_t));
+    const size_t o_ident = align16(o_upre + pl.uprefix.size() * sizeof(int64_t));
+    const size_t o_upre1 = align16(o_ident + pl.ident.size() * sizeof(int32_t));
+    const size_t o_lmin = align16(o_upre1 + pl.uprefix1.size() * sizeof(int64_t));
     const size_t o_hoff = align16(o_lmin + (size_t)n_lmin * sizeof(int32_t));
     const size_t total = align16(o_hoff + (hoff ? (size_t)(pl.S + 1) * sizeof(int64_t) : 0));
 
@@ -254,6 +285,10 @@ int upload_plan(rqa_ctx *c, Plan &pl, const int32_t *lmin, int n_lmin, const int
     if (!pl.T.empty()) std::memcpy(h + o_T, pl.T.data(), pl.T.size() * sizeof(uint64_t));
     std::memcpy(h + o_lpt, pl.items_lpt.data(), pl.items_lpt.size() * sizeof(Item));
     std::memcpy(h + o_ser, pl.items_ser.data(), pl.items_ser.size() * sizeof(Item));
+    std::memcpy(h + o_order, pl.order.data(), pl.order.size() * sizeof(int32_t));
+    std::memcpy(h + o_upre, pl.uprefix.data(), pl.uprefix.size() * sizeof(int64_t));
+    std::memcpy(h + o_ident, pl.ident.data(), pl.ident.size() * sizeof(int32_t));
+    std::memcpy(h + o_upre1, pl.uprefix1.data(), pl.uprefix1.size() * sizeof(int64_t));
     if (n_lmin) std::memcpy(h + o_lmin, lmin, (size_t)n_lmin * sizeof(int32_t));
     if (hoff) std::memcpy(h + o_hoff, hoff, (size_t)(pl.S + 1) * sizeof(int64_t));
     char *d = static_cast<char *>(c->arena.p);
@@ -264,6 +299,10 @@ int upload_plan(rqa_ctx *c, Plan &pl, const int32_t *lmin, int n_lmin, const int
     pl.d_T = reinterpret_cast<uint64_t *>(d + o_T);
     pl.d_lpt = reinterpret_cast<Item *>(d + o_lpt);
     pl.d_ser = reinterpret_cast<Item *>(d + o_ser);
+    pl.d_order = reinterpret_cast<int32_t *>(d + o_order);
+    pl.d_uprefix = reinterpret_cast<int64_t *>(d + o_upre);
+    pl.d_ident = reinterpret_cast<int32_t *>(d + o_ident);
+    pl.d_uprefix1 = reinterpret_cast<int64_t *>(d + o_upre1);
     pl.d_lmin = reinterpret_cast<int32_t *>(d + o_lmin);
     pl.d_hoff = reinterpret_cast<int64_t *>(d + o_hoff);
     return RQA_OK;
@@ -412,25 +451,31 @@ int run_lines(rqa_ctx *c, const Plan &pl, const float *eps, uint64_t *hist, cons
     a.band = c->band;
     a.status = P<int>(c->status);
     unsigned *q = nullptr;
+    const int full_grid = persistent_grid(c, (size_t)1 << 30);
+    auto grid_for = [&](int64_t units) {
+        return (int)std::max<int64_t>(1, std::min<int64_t>(full_grid, (units + WARPS - 1) / WARPS));
+    };
     if (c->schedule == RQA_SCHED_PER_SERIES) {
         if (int rc = reset_queue(c, S, &q)) return rc;
         for (int s = 0; s < S; ++s) {
-            const int ib = pl.ser_begin[s], ie = pl.ser_begin[s + 1];
-            a.items = pl.d_ser + ib;
-            a.n_items = ie - ib;
+            a.order = pl.d_ident + s;
+            a.uprefix = pl.d_uprefix1 + 2 * (size_t)s;
+            a.n_pos = 1;
+            a.n_units = pl.sd[s].nbands;
             a.queue = q;
             q += 16;
-            if (int rc = launched(c, launch_lines(a, lb, K, persistent_grid(c, (size_t)a.n_items),
-                                                  pl.mt, c->stream)))
+            if (int rc = launched(c, launch_lines(a, lb, K, grid_for(a.n_units), pl.mt, c->stream)))
                 return rc;
         }
         return RQA_OK;
     }
     if (int rc = reset_queue(c, 1, &q)) return rc;
-    a.items = pl.d_lpt;
-    a.n_items = (int)pl.items_lpt.size();
+    a.order = pl.d_order;
+    a.uprefix = pl.d_uprefix;
+    a.n_pos = S;
+    a.n_units = pl.uprefix[S];
     a.queue = q;
-    return launched(c, launch_lines(a, lb, K, persistent_grid(c, (size_t)a.n_items), pl.mt, c->stream));
+    return launched(c, launch_lines(a, lb, K, grid_for(a.n_units), pl.mt, c->stream));
 }
 
 // Line pass plus the requested outputs.  hist/hoff come from the caller.

@@ -23,8 +23,6 @@ namespace rqa {
 
 constexpr int HS_STRIDE = LSH + 1;  // +1: spreads lanes of one length over banks
 
-int lines_smem_bytes(int K) { return K * HS_STRIDE * 4; }
-
 template <bool HIST>
 struct LineSink {
     uint32_t *hs;           // shared [K][HS_STRIDE], index = length
@@ -71,15 +69,35 @@ __device__ __forceinline__ void runs_word(uint32_t w, uint32_t &c, Sink &sink)
     c = tl;
 }
 
-template <int D, int M, bool HIST>
+// Per-warp shared memory: the warp's own short-line histogram and thresholds.
+__host__ __device__ constexpr int warp_smem_words(int K) { return K * HS_STRIDE + 32; }
+
+int lines_smem_bytes(int K) { return WARPS * warp_smem_words(K) * 4; }
+
+// Series s and band b of work unit u: units are the bands of the series in
+// a.order (largest series first), band 0 (longest diagonals) first.
+__device__ __forceinline__ void unit_of(const CellArgs &a, int64_t u, int &s, int &b)
+{
+    int lo = 0, hi = a.n_pos;  // last pos with uprefix[pos] <= u
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (a.uprefix[mid] <= u) lo = mid;
+        else hi = mid;
+    }
+    s = a.order[lo];
+    b = (int)(u - a.uprefix[lo]);
+}
+
+// Warp-centric: every warp pulls whole bands from one global queue and keeps
+// its own histogram in shared memory, flushed when it moves to another series
+// and at exit.  No CTA-wide barrier, so no warp waits for another.
+template <int D, int M, int TAU, bool HIST>
 __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int K)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t *hs = reinterpret_cast<uint32_t *>(smem);
-    __shared__ uint32_t epsb[32];
-    __shared__ int slot;
-    __shared__ int bad;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *hs = reinterpret_cast<uint32_t *>(smem) + warp * warp_smem_words(K);
+    uint32_t *epsb = hs + K * HS_STRIDE;
     const bool klane = lane < K;
 
     // lane k's bits as masks, for the bit-sliced test r <= k
@@ -87,104 +105,31 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
 #pragma unroll
     for (int b = 0; b < 5; ++b) km[b] = ((lane >> b) & 1) ? FULL : 0u;
 
-    for (int x = threadIdx.x; x < K * HS_STRIDE; x += THREADS) hs[x] = 0;
+    for (int x = lane; x < K * HS_STRIDE; x += 32) hs[x] = 0;
+    __syncwarp();
 
-    for (;;) {
-        const int it = next_item(a.queue, a.n_items, &slot);
-        if (it < 0) break;
-        const Item item = a.items[it];
-        const SeriesDev sd = a.series[item.s];
-        if (warp == 0) {
-            uint32_t v = 0xffffffffu;   // padding: above every key
-            bool ok = true;
-            if (klane) {
-                v = __float_as_uint(lb.eps[(int64_t)item.s * K + lane]);
-                if (v == 0x80000000u) v = 0u;                        // -0 == +0
-                if ((v & 0x80000000u) || v > 0x7f800000u) ok = false;  // negative or NaN
-            }
-            const uint32_t prev = __shfl_up_sync(FULL, v, 1);
-            if (klane && lane > 0 && prev > v) ok = false;           // not ascending
-            const bool all_ok = __all_sync(FULL, ok);
-            epsb[lane] = v;
-            if (lane == 0) {
-                bad = !all_ok;
-                if (!all_ok) set_status(a.status, 8 /*UNSORTED*/);
-            }
-        }
-        __syncthreads();
-        if (bad) continue;
+    int cur = -1;
+    bool bad = false;
+    SeriesDev sd{};
+    uint64_t cnt = 0;
+    LineSink<HIST> sink;
+    sink.hs = hs + lane * HS_STRIDE;
+    sink.hist = nullptr;
+    sink.lmax = 0;
 
-        const float *ys = a.y + sd.off;
-        uint64_t cnt = 0;
-        LineSink<HIST> sink;
-        sink.hs = hs + lane * HS_STRIDE;
-        sink.hist = nullptr;
-        if (HIST && klane)
-            sink.hist = lb.hist + lb.hist_off[item.s] + (int64_t)lane * (sd.ne - 1);
-        sink.lmax = 0;
-
-        for (int b = item.b_lo + warp; b < item.b_hi; b += WARPS) {
-            int d_lo, d_hi;
-            band_range(b, a.band, sd.ne, d_lo, d_hi);
-            const int rows = sd.ne - d_lo;
-            uint32_t carry[D];
-#pragma unroll
-            for (int j = 0; j < D; ++j) carry[j] = 0;
-            for (int i0 = 0; i0 < rows; i0 += 32) {
-                const int i = i0 + lane;
-                RowVec<M> rv;
-                if (i < rows) rv.load(ys, i, sd.tau, sd.m);
-#pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    const int dl = d_lo + j;
-                    uint32_t r = 31;  // outside the diagonal: recurrent for no k
-                    if (i < sd.ne - dl) {
-                        const uint32_t key =
-                            __float_as_uint(rv.dist(ys, i, i + dl, sd.tau, sd.m));
-                        r = 0;
-                        r += (epsb[r + 15] < key) ? 16u : 0u;
-                        r += (epsb[r + 7] < key) ? 8u : 0u;
-                        r += (epsb[r + 3] < key) ? 4u : 0u;
-                        r += (epsb[r + 1] < key) ? 2u : 0u;
-                        r += (epsb[r] < key) ? 1u : 0u;
-                    }
-                    const uint32_t B0 = __ballot_sync(FULL, r & 1u);
-                    const uint32_t B1 = __ballot_sync(FULL, r & 2u);
-                    const uint32_t B2 = __ballot_sync(FULL, r & 4u);
-                    const uint32_t B3 = __ballot_sync(FULL, r & 8u);
-                    const uint32_t B4 = __ballot_sync(FULL, r & 16u);
-                    if (klane) {
-                        // gt = {t : r_t > k}, most significant bit plane first
-                        uint32_t gt = B4 & ~km[4];
-                        uint32_t eq = ~(B4 ^ km[4]);
-                        gt |= eq & B3 & ~km[3];
-                        eq &= ~(B3 ^ km[3]);
-                        gt |= eq & B2 & ~km[2];
-                        eq &= ~(B2 ^ km[2]);
-                        gt |= eq & B1 & ~km[1];
-                        eq &= ~(B1 ^ km[1]);
-                        gt |= eq & B0 & ~km[0];
-                        const uint32_t w = ~gt;
-                        cnt += __popc(w);
-                        runs_word(w, carry[j], sink);
-                    }
-                }
-            }
-            if (klane) {
-#pragma unroll
-                for (int j = 0; j < D; ++j)
-                    if (carry[j]) sink.emit(carry[j]);
-            }
-        }
+    auto flush = [&]() {
+        if (cur < 0) return;
         if (klane) {
-            const int64_t o = (int64_t)item.s * K + lane;
+            const int64_t o = (int64_t)cur * K + lane;
             if (cnt) atomicAdd(reinterpret_cast<unsigned long long *>(lb.count + o),
                                (unsigned long long)cnt);
             if (sink.lmax) atomicMax(lb.lmax + o, sink.lmax);
         }
-        __syncthreads();
-        uint64_t *gs = lb.hshort + (int64_t)item.s * K * LSH;
-        for (int x = threadIdx.x; x < K * LSH; x += THREADS) {
+        cnt = 0;
+        sink.lmax = 0;
+        __syncwarp();
+        uint64_t *gs = lb.hshort + (int64_t)cur * K * LSH;
+        for (int x = lane; x < K * LSH; x += 32) {
             const int k = x / LSH, l = x - k * LSH + 1;
             const uint32_t v = hs[k * HS_STRIDE + l];
             if (v) {
@@ -192,20 +137,107 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
                 hs[k * HS_STRIDE + l] = 0;
             }
         }
+        __syncwarp();
+    };
+
+    for (;;) {
+        int64_t u = 0;
+        if (lane == 0) u = (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(a.queue), 1ull);
+        u = __shfl_sync(FULL, u, 0);
+        if (u >= a.n_units) break;
+        int s, b;
+        unit_of(a, u, s, b);
+        if (s != cur) {
+            flush();
+            cur = s;
+            sd = a.series[s];
+            uint32_t v = 0xffffffffu;   // padding: above every key
+            bool ok = true;
+            if (klane) {
+                v = __float_as_uint(lb.eps[(int64_t)s * K + lane]);
+                if (v == 0x80000000u) v = 0u;                           // -0 == +0
+                if ((v & 0x80000000u) || v > 0x7f800000u) ok = false;  // negative or NaN
+            }
+            const uint32_t prev = __shfl_up_sync(FULL, v, 1);
+            if (klane && lane > 0 && prev > v) ok = false;              // not ascending
+            bad = !__all_sync(FULL, ok);
+            epsb[lane] = v;
+            if (bad && lane == 0) set_status(a.status, 8 /*UNSORTED*/);
+            if (HIST && klane)
+                sink.hist = lb.hist + lb.hist_off[s] + (int64_t)lane * (sd.ne - 1);
+            __syncwarp();
+        }
+        if (bad) continue;
+
+        const float *ys = a.y + sd.off;
+        int d_lo, d_hi;
+        band_range(b, D, sd.ne, d_lo, d_hi);
+        const int rows = sd.ne - d_lo;
+        uint32_t carry[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) carry[j] = 0;
+        for (int i0 = 0; i0 < rows; i0 += 32) {
+            const int i = i0 + lane;
+            BandTile<M, TAU, D> tile;
+            tile.load(ys, sd.n, i, d_lo, rows, sd.tau, sd.m);
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const int dl = d_lo + j;
+                uint32_t r = 31;  // outside the diagonal: recurrent for no k
+                if (i < sd.ne - dl) {
+                    const uint32_t key = __float_as_uint(tile.dist(ys, j, i, dl, sd.tau, sd.m));
+                    r = 0;
+                    r += (epsb[r + 15] < key) ? 16u : 0u;
+                    r += (epsb[r + 7] < key) ? 8u : 0u;
+                    r += (epsb[r + 3] < key) ? 4u : 0u;
+                    r += (epsb[r + 1] < key) ? 2u : 0u;
+                    r += (epsb[r] < key) ? 1u : 0u;
+                }
+                const uint32_t B0 = __ballot_sync(FULL, r & 1u);
+                const uint32_t B1 = __ballot_sync(FULL, r & 2u);
+                const uint32_t B2 = __ballot_sync(FULL, r & 4u);
+                const uint32_t B3 = __ballot_sync(FULL, r & 8u);
+                const uint32_t B4 = __ballot_sync(FULL, r & 16u);
+                if (klane) {
+                    // gt = {t : r_t > k}, most significant bit plane first
+                    uint32_t gt = B4 & ~km[4];
+                    uint32_t eq = ~(B4 ^ km[4]);
+                    gt |= eq & B3 & ~km[3];
+                    eq &= ~(B3 ^ km[3]);
+                    gt |= eq & B2 & ~km[2];
+                    eq &= ~(B2 ^ km[2]);
+                    gt |= eq & B1 & ~km[1];
+                    eq &= ~(B1 ^ km[1]);
+                    gt |= eq & B0 & ~km[0];
+                    const uint32_t w = ~gt;
+                    cnt += __popc(w);
+                    runs_word(w, carry[j], sink);
+                }
+            }
+        }
+        if (klane) {
+#pragma unroll
+            for (int j = 0; j < D; ++j)
+                if (carry[j]) sink.emit(carry[j]);
+        }
     }
+    flush();
 }
 
-template <int D, bool HIST>
-static cudaError_t launch_lines_dm(const CellArgs &a, const LineBufs &lb, int K, int grid,
-                                   int max_m, cudaStream_t st)
+template <bool HIST>
+static cudaError_t launch_lines_h(const CellArgs &a, const LineBufs &lb, int K, int grid,
+                                 int embed, cudaStream_t st)
 {
     void (*kern)(CellArgs, LineBufs, int);
-    switch (max_m) {
-    case 1: kern = k_lines<D, 1, HIST>; break;
-    case 2: kern = k_lines<D, 2, HIST>; break;
-    case 3: kern = k_lines<D, 3, HIST>; break;
-    case 4: kern = k_lines<D, 4, HIST>; break;
-    default: kern = k_lines<D, 0, HIST>; break;
+    switch (embed) {
+    case E_M1T1: kern = k_lines<BAND, 1, 1, HIST>; break;
+    case E_M3T1: kern = k_lines<BAND, 3, 1, HIST>; break;
+    case E_M3T3: kern = k_lines<BAND, 3, 3, HIST>; break;
+    case E_M1: kern = k_lines<BAND, 1, 0, HIST>; break;
+    case E_M2: kern = k_lines<BAND, 2, 0, HIST>; break;
+    case E_M3: kern = k_lines<BAND, 3, 0, HIST>; break;
+    case E_M4: kern = k_lines<BAND, 4, 0, HIST>; break;
+    default: kern = k_lines<BAND, 0, 0, HIST>; break;
     }
     const int smem = lines_smem_bytes(K);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -214,17 +246,17 @@ static cudaError_t launch_lines_dm(const CellArgs &a, const LineBufs &lb, int K,
     return cudaGetLastError();
 }
 
-cudaError_t launch_lines(const CellArgs &a, const LineBufs &lb, int K, int grid, int max_m,
+cudaError_t launch_lines(const CellArgs &a, const LineBufs &lb, int K, int grid, int embed,
                          cudaStream_t st)
 {
     const bool hist = lb.hist != nullptr;
-    if (a.band != 16) return cudaErrorInvalidValue;
-    if (!a.y || !a.series || !a.items || !a.queue || !a.status || !lb.eps || !lb.count ||
-        !lb.lmax || !lb.hshort || (hist && !lb.hist_off) || K < 1 || K > KMAX || grid < 1 ||
-        a.n_items < 1)
+    if (a.band != BAND) return cudaErrorInvalidValue;
+    if (!a.y || !a.series || !a.order || !a.uprefix || !a.queue || !a.status || !lb.eps ||
+        !lb.count || !lb.lmax || !lb.hshort || (hist && !lb.hist_off) || K < 1 || K > KMAX ||
+        grid < 1 || a.n_units < 1 || a.n_pos < 1)
         return cudaErrorInvalidValue;
-    return hist ? launch_lines_dm<16, true>(a, lb, K, grid, max_m, st)
-                : launch_lines_dm<16, false>(a, lb, K, grid, max_m, st);
+    return hist ? launch_lines_h<true>(a, lb, K, grid, embed, st)
+                : launch_lines_h<false>(a, lb, K, grid, embed, st);
 }
 
 // DET_k(lmin) = (C_k - sum_{l < lmin} l P_k(l)) / C_k  (Eq. 4), an FP64 ratio of

@@ -14,21 +14,58 @@ __device__ __forceinline__ void set_status(int *status, int code)
     atomicCAS(status, 0, code);
 }
 
-// Row vector x_i = (y[i], y[i+tau], ..., y[i+(m-1)tau]) held in registers for
-// a compile-time embedding dimension M (M == 0: generic, re-read per cell).
-template <int M>
-struct RowVec {
+// Distances of one lane's cells in a band: row i (lane), diagonals
+// d_lo .. d_lo+D-1.  Maximum-norm distance (Sect. 2) with FP32 subtract, abs
+// and max only, so every value is exact and equal to a CPU evaluation.
+//
+// Compile-time embedding (M >= 1, TAU >= 1): the row vector
+// x_i = (y[i], y[i+TAU], ...) and the column window y[i+d_lo .. i+d_lo+D-1+
+// (M-1)TAU] are loaded into registers once per 32-row block, so the D cells of
+// the lane need no further memory traffic.
+template <int M, int TAU, int D>
+struct BandTile {
     float a[M];
-    __device__ __forceinline__ void load(const float *__restrict__ ys, int i, int tau, int)
+    float w[D + (M - 1) * TAU];
+    __device__ __forceinline__ void load(const float *__restrict__ ys, int n, int i, int d_lo,
+                                         int rows, int, int)
     {
+        if (i < rows) {
 #pragma unroll
-        for (int q = 0; q < M; ++q) a[q] = __ldg(ys + i + q * tau);
+            for (int q = 0; q < M; ++q) a[q] = __ldg(ys + i + q * TAU);
+        }
+#pragma unroll
+        for (int x = 0; x < D + (M - 1) * TAU; ++x) {
+            const int idx = i + d_lo + x;
+            w[x] = (i < rows && idx < n) ? __ldg(ys + idx) : 0.f;
+        }
     }
-    // Maximum-norm distance to x_j (Sect. 2): FP32 subtract, abs and max only,
-    // so the result is exact and identical to a CPU evaluation.
-    __device__ __forceinline__ float dist(const float *__restrict__ ys, int i, int j, int tau,
+    // cell (i, i + d_lo + j); only called for cells inside the triangle
+    __device__ __forceinline__ float dist(const float *__restrict__, int j, int, int, int,
                                           int) const
     {
+        float d = fabsf(a[0] - w[j]);
+#pragma unroll
+        for (int q = 1; q < M; ++q) d = fmaxf(d, fabsf(a[q] - w[j + q * TAU]));
+        return d;
+    }
+};
+
+// Compile-time M, run-time tau: the row vector in registers, columns read per cell.
+template <int M, int D>
+struct BandTile<M, 0, D> {
+    float a[M];
+    __device__ __forceinline__ void load(const float *__restrict__ ys, int, int i, int,
+                                         int rows, int tau, int)
+    {
+        if (i < rows) {
+#pragma unroll
+            for (int q = 0; q < M; ++q) a[q] = __ldg(ys + i + q * tau);
+        }
+    }
+    __device__ __forceinline__ float dist(const float *__restrict__ ys, int, int i, int dl,
+                                          int tau, int) const
+    {
+        const int j = i + dl;
         float d = fabsf(a[0] - __ldg(ys + j));
 #pragma unroll
         for (int q = 1; q < M; ++q) d = fmaxf(d, fabsf(a[q] - __ldg(ys + j + q * tau)));
@@ -36,18 +73,24 @@ struct RowVec {
     }
 };
 
-template <>
-struct RowVec<0> {
-    __device__ __forceinline__ void load(const float *, int, int, int) {}
-    __device__ __forceinline__ float dist(const float *__restrict__ ys, int i, int j, int tau,
-                                          int m) const
+// Generic embedding: everything read per cell.
+template <int D>
+struct BandTile<0, 0, D> {
+    __device__ __forceinline__ void load(const float *, int, int, int, int, int, int) {}
+    __device__ __forceinline__ float dist(const float *__restrict__ ys, int, int i, int dl,
+                                          int tau, int m) const
     {
+        const int j = i + dl;
         float d = fabsf(__ldg(ys + i) - __ldg(ys + j));
         for (int q = 1; q < m; ++q)
             d = fmaxf(d, fabsf(__ldg(ys + i + q * tau) - __ldg(ys + j + q * tau)));
         return d;
     }
 };
+
+// Embedding variants with their own kernel instantiation.
+enum Embed : int { E_GENERIC = 0, E_M1 = 1, E_M2 = 2, E_M3 = 3, E_M4 = 4,
+                   E_M1T1 = 11, E_M3T1 = 31, E_M3T3 = 33 };
 
 // Fetch the next work item for this CTA (one atomic per CTA), -1 when done.
 __device__ __forceinline__ int next_item(unsigned int *queue, int n_items, int *sh_slot)

@@ -17,6 +17,7 @@ constexpr int NSUB_MAX = 24;       // bracket-subdivided coarse buckets per seri
 constexpr int LSH = 128;           // line lengths 1..LSH counted in shared memory
 constexpr int LMIN_MAX = 8;        // entries of an lmin list
 constexpr int THREADS = 256;       // threads per CTA of the cell kernels
+constexpr int BAND = 16;           // diagonals per warp band
 constexpr int WARPS = THREADS / 32;
 
 // Counting rounds of the selection.
@@ -60,17 +61,24 @@ struct SelBufs {
 struct CellArgs {
     const float *y;
     const SeriesDev *series;
+    // CTA-level work (counting rounds): items of bands
     const Item *items;
     int32_t n_items;
     int32_t band;
-    unsigned int *queue;   // persistent-CTA ticket counter, zeroed before launch
+    // warp-level work (line pass): every band of the series order[0..n_pos)
+    const int32_t *order;    // series, largest first
+    const int64_t *uprefix;  // n_pos + 1 prefix of band counts along order
+    int32_t n_pos;
+    int64_t n_units;
+    unsigned int *queue;   // ticket counter (64-bit aligned), zeroed before launch
     int *status;
 };
 
 // Kernels (launch wrappers return cudaGetLastError()).
 cudaError_t launch_check_finite(const float *y, int64_t n, int *status, cudaStream_t st);
+// embed: the Embed code of the batch (rqa_common.cuh), picks the distance kernel variant.
 cudaError_t launch_count(int round, const CellArgs &a, const SelBufs &sb, int K, int grid,
-                         int max_m, cudaStream_t st);
+                         int embed, cudaStream_t st);
 cudaError_t launch_select(int round, const SelBufs &sb, const SeriesDev *series, int s_begin,
                           int n_series, int K, float *eps_out, uint64_t *le_out,
                           uint64_t *lt_out, int *status, cudaStream_t st);
@@ -83,7 +91,7 @@ struct LineBufs {
     uint64_t *hist;        // caller's full histogram or nullptr
     const int64_t *hist_off;  // device [S+1] offsets into hist (nullptr if no hist)
 };
-cudaError_t launch_lines(const CellArgs &a, const LineBufs &lb, int K, int grid, int max_m,
+cudaError_t launch_lines(const CellArgs &a, const LineBufs &lb, int K, int grid, int embed,
                          cudaStream_t st);
 cudaError_t launch_finalize_det(const LineBufs &lb, const SeriesDev *series, int S, int K,
                                 const int32_t *lmin_dev, int n_lmin, double *det,

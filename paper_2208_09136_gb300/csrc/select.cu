@@ -70,19 +70,20 @@ __device__ __forceinline__ int bin_of(uint32_t key, const int8_t *t1, const int8
 // One persistent launch over the work items; each CTA histograms the keys of
 // its item's bands in shared memory and adds the non-zero bins to the
 // series' 64-bit global histogram at the end of the item.
-template <int ROUND, int M>
+template <int ROUND, int M, int TAU>
 __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int slot;
     __shared__ int nb_used_sh;
+    __shared__ int next_band;
     const int nbins_max = (ROUND == R_COARSE) ? NCOARSE
                         : (ROUND == R_COARSE_SUB) ? NCOARSE + NSUB_MAX * NFINE
                                                   : K * NFINE;
     uint32_t *h = reinterpret_cast<uint32_t *>(smem);
     int8_t *t1 = reinterpret_cast<int8_t *>(h + nbins_max);
     int8_t *t2 = t1 + NCOARSE;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
 
     for (int x = threadIdx.x; x < nbins_max; x += THREADS) h[x] = 0;
 
@@ -98,6 +99,7 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
             else if (ROUND == R_MID) nb = sb.n_mid[item.s] * NFINE;
             else nb = sb.n_fin[item.s] * NFINE;
             nb_used_sh = nb;
+            next_band = item.b_lo;
         }
         __syncthreads();
         const int nb_used = nb_used_sh;
@@ -115,19 +117,28 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
         }
 
         const float *ys = a.y + sd.off;
-        for (int b = item.b_lo + warp; b < item.b_hi; b += WARPS) {
+        for (;;) {
+            // bands are handed to warps one at a time, so no warp idles while
+            // another still has several bands of the item left
+            int b = 0;
+            if (lane == 0) b = atomicAdd(&next_band, 1);
+            b = __shfl_sync(FULL, b, 0);
+            if (b >= item.b_hi) break;
             int d_lo, d_hi;
-            band_range(b, a.band, sd.ne, d_lo, d_hi);
+            band_range(b, BAND, sd.ne, d_lo, d_hi);
             const int rows = sd.ne - d_lo;
             int last = -1;
             uint32_t run = 0;
             for (int i0 = 0; i0 < rows; i0 += 32) {
                 const int i = i0 + lane;
-                RowVec<M> rv;
-                if (i < rows) rv.load(ys, i, sd.tau, sd.m);
-                for (int dl = d_lo; dl < d_hi; ++dl) {
+                BandTile<M, TAU, BAND> tile;
+                tile.load(ys, sd.n, i, d_lo, rows, sd.tau, sd.m);
+#pragma unroll
+                for (int j = 0; j < BAND; ++j) {
+                    const int dl = d_lo + j;
                     if (i < sd.ne - dl) {
-                        const uint32_t key = __float_as_uint(rv.dist(ys, i, i + dl, sd.tau, sd.m));
+                        const uint32_t key =
+                            __float_as_uint(tile.dist(ys, j, i, dl, sd.tau, sd.m));
                         const int bin = bin_of<ROUND>(key, t1, t2);
                         if (bin >= 0) {
                             // consecutive cells of a lane are neighbours in the
@@ -159,16 +170,19 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
 
 template <int ROUND>
 static cudaError_t launch_count_m(const CellArgs &a, const SelBufs &sb, int K, int grid,
-                                  int max_m, cudaStream_t st)
+                                  int embed, cudaStream_t st)
 {
     const int smem = count_smem_bytes(ROUND, K);
     void (*kern)(CellArgs, SelBufs, int);
-    switch (max_m) {
-    case 1: kern = k_count<ROUND, 1>; break;
-    case 2: kern = k_count<ROUND, 2>; break;
-    case 3: kern = k_count<ROUND, 3>; break;
-    case 4: kern = k_count<ROUND, 4>; break;
-    default: kern = k_count<ROUND, 0>; break;
+    switch (embed) {
+    case E_M1T1: kern = k_count<ROUND, 1, 1>; break;
+    case E_M3T1: kern = k_count<ROUND, 3, 1>; break;
+    case E_M3T3: kern = k_count<ROUND, 3, 3>; break;
+    case E_M1: kern = k_count<ROUND, 1, 0>; break;
+    case E_M2: kern = k_count<ROUND, 2, 0>; break;
+    case E_M3: kern = k_count<ROUND, 3, 0>; break;
+    case E_M4: kern = k_count<ROUND, 4, 0>; break;
+    default: kern = k_count<ROUND, 0, 0>; break;
     }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -177,16 +191,16 @@ static cudaError_t launch_count_m(const CellArgs &a, const SelBufs &sb, int K, i
 }
 
 cudaError_t launch_count(int round, const CellArgs &a, const SelBufs &sb, int K, int grid,
-                         int max_m, cudaStream_t st)
+                         int embed, cudaStream_t st)
 {
     if (!a.y || !a.series || !a.items || !a.queue || !a.status || !sb.hist || K < 1 || K > KMAX ||
-        grid < 1 || a.n_items < 1)
+        grid < 1 || a.n_items < 1 || a.band != BAND)
         return cudaErrorInvalidValue;
     switch (round) {
-    case R_COARSE: return launch_count_m<R_COARSE>(a, sb, K, grid, max_m, st);
-    case R_COARSE_SUB: return launch_count_m<R_COARSE_SUB>(a, sb, K, grid, max_m, st);
-    case R_MID: return launch_count_m<R_MID>(a, sb, K, grid, max_m, st);
-    default: return launch_count_m<R_FINAL>(a, sb, K, grid, max_m, st);
+    case R_COARSE: return launch_count_m<R_COARSE>(a, sb, K, grid, embed, st);
+    case R_COARSE_SUB: return launch_count_m<R_COARSE_SUB>(a, sb, K, grid, embed, st);
+    case R_MID: return launch_count_m<R_MID>(a, sb, K, grid, embed, st);
+    default: return launch_count_m<R_FINAL>(a, sb, K, grid, embed, st);
     }
 }
 
