@@ -82,9 +82,11 @@ struct Plan {
     std::vector<Item> items_ser;             // grouped by series
     std::vector<int> ser_begin;              // S+1 into items_ser
     std::vector<int32_t> order;              // series by size, largest first
-    std::vector<int64_t> uprefix;            // S+1 band-count prefix along order
+    std::vector<int64_t> uprefix;            // S+1 unit-count prefix along order
+    int32_t chunk = 1;                       // bands per line-pass unit (batched)
     std::vector<int32_t> ident;              // 0..S-1
-    std::vector<int64_t> uprefix1;           // [2s], [2s+1] = 0, bands of s
+    std::vector<int64_t> uprefix1;           // [2s], [2s+1] = 0, units of s alone
+    std::vector<int32_t> chunk1;             // bands per unit of s alone
     // device pointers into the arena after upload
     SeriesDev *d_sd = nullptr;
     uint64_t *d_T = nullptr;
@@ -173,6 +175,13 @@ int validate_rr(const int32_t *rr_num, int32_t rr_den, int32_t K)
     return RQA_OK;
 }
 
+int persistent_grid(rqa_ctx *c, size_t n_items)
+{
+    const int bpsm = c->bpsm > 0 ? c->bpsm : 2;
+    const size_t g = (size_t)c->sm_count * bpsm;
+    return (int)std::max<size_t>(1, std::min(g, n_items));
+}
+
 int make_plan(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_den, int K,
               Plan &pl)
 {
@@ -233,19 +242,31 @@ int make_plan(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_
         build_items(pl.sd[s], s, c->band, t, 4 * WARPS, pl.items_ser, nullptr);
         pl.ser_begin[s + 1] = (int)pl.items_ser.size();
     }
-    // warp work units (line pass): every band, series largest first
+    // warp work units (line pass): runs of `chunk` bands, series largest
+    // first; about eight units per warp so the tail stays short while each
+    // unit's histogram flush is spread over many cells
+    const int64_t n_warps = (int64_t)persistent_grid(c, (size_t)1 << 30) * WARPS;
+    auto chunk_for = [&](int64_t bands) {
+        return (int32_t)std::max<int64_t>(4, std::min<int64_t>(64, bands / (n_warps * 8)));
+    };
+    int64_t total_bands = 0;
+    for (int s = 0; s < S; ++s) total_bands += pl.sd[s].nbands;
+    pl.chunk = chunk_for(total_bands);
     pl.order.resize(S);
     for (int s = 0; s < S; ++s) pl.order[s] = s;
     std::stable_sort(pl.order.begin(), pl.order.end(),
                      [&](int x, int y) { return pl.sd[x].P > pl.sd[y].P; });
     pl.uprefix.assign(S + 1, 0);
-    for (int i = 0; i < S; ++i) pl.uprefix[i + 1] = pl.uprefix[i] + pl.sd[pl.order[i]].nbands;
+    for (int i = 0; i < S; ++i)
+        pl.uprefix[i + 1] = pl.uprefix[i] + (pl.sd[pl.order[i]].nbands + pl.chunk - 1) / pl.chunk;
     pl.ident.resize(S);
     pl.uprefix1.resize(2 * (size_t)S);
+    pl.chunk1.resize(S);
     for (int s = 0; s < S; ++s) {
         pl.ident[s] = s;
+        pl.chunk1[s] = chunk_for(pl.sd[s].nbands);
         pl.uprefix1[2 * s] = 0;
-        pl.uprefix1[2 * s + 1] = pl.sd[s].nbands;
+        pl.uprefix1[2 * s + 1] = (pl.sd[s].nbands + pl.chunk1[s] - 1) / pl.chunk1[s];
     }
     return RQA_OK;
 }
@@ -351,12 +372,6 @@ SelBufs sel_bufs(rqa_ctx *c, const Plan &pl)
     return sb;
 }
 
-int persistent_grid(rqa_ctx *c, size_t n_items)
-{
-    const int bpsm = c->bpsm > 0 ? c->bpsm : 2;
-    const size_t g = (size_t)c->sm_count * bpsm;
-    return (int)std::max<size_t>(1, std::min(g, n_items));
-}
 
 // Zero the queue tickets of n launches; returns the first ticket pointer.
 int reset_queue(rqa_ctx *c, int n, unsigned **q)
@@ -461,7 +476,8 @@ int run_lines(rqa_ctx *c, const Plan &pl, const float *eps, uint64_t *hist, cons
             a.order = pl.d_ident + s;
             a.uprefix = pl.d_uprefix1 + 2 * (size_t)s;
             a.n_pos = 1;
-            a.n_units = pl.sd[s].nbands;
+            a.chunk = pl.chunk1[s];
+            a.n_units = pl.uprefix1[2 * (size_t)s + 1];
             a.queue = q;
             q += 16;
             if (int rc = launched(c, launch_lines(a, lb, K, grid_for(a.n_units), pl.mt, c->stream)))
@@ -473,6 +489,7 @@ int run_lines(rqa_ctx *c, const Plan &pl, const float *eps, uint64_t *hist, cons
     a.order = pl.d_order;
     a.uprefix = pl.d_uprefix;
     a.n_pos = S;
+    a.chunk = pl.chunk;
     a.n_units = pl.uprefix[S];
     a.queue = q;
     return launched(c, launch_lines(a, lb, K, grid_for(a.n_units), pl.mt, c->stream));

@@ -25,13 +25,13 @@ constexpr int HS_STRIDE = LSH + 1;  // +1: spreads lanes of one length over bank
 
 template <bool HIST>
 struct LineSink {
-    uint32_t *hs;           // shared [K][HS_STRIDE], index = length
+    uint32_t *hs;           // this lane's row of the warp's shared histogram, index = length
     uint64_t *hist;         // this series' full histogram row for lane k, or null
     uint32_t lmax;
     __device__ __forceinline__ void emit(uint32_t len)
     {
         if (len <= (uint32_t)LSH) {
-            atomicAdd(hs + len, 1u);
+            hs[len] += 1u;  // the row belongs to this lane alone
         } else if (HIST) {
             atomicAdd(reinterpret_cast<unsigned long long *>(hist + (len - 1)), 1ull);
         }
@@ -74,9 +74,11 @@ __host__ __device__ constexpr int warp_smem_words(int K) { return K * HS_STRIDE 
 
 int lines_smem_bytes(int K) { return WARPS * warp_smem_words(K) * 4; }
 
-// Series s and band b of work unit u: units are the bands of the series in
-// a.order (largest series first), band 0 (longest diagonals) first.
-__device__ __forceinline__ void unit_of(const CellArgs &a, int64_t u, int &s, int &b)
+// Series s and bands [b_lo, b_hi) of work unit u: a unit is a.chunk
+// consecutive bands of one series; units run over the series in a.order
+// (largest first), band 0 (longest diagonals) first.
+__device__ __forceinline__ void unit_of(const CellArgs &a, int64_t u, int &s, int &b_lo,
+                                        int &b_hi, const SeriesDev *series)
 {
     int lo = 0, hi = a.n_pos;  // last pos with uprefix[pos] <= u
     while (hi - lo > 1) {
@@ -85,7 +87,8 @@ __device__ __forceinline__ void unit_of(const CellArgs &a, int64_t u, int &s, in
         else hi = mid;
     }
     s = a.order[lo];
-    b = (int)(u - a.uprefix[lo]);
+    b_lo = (int)(u - a.uprefix[lo]) * a.chunk;
+    b_hi = min(b_lo + a.chunk, series[s].nbands);
 }
 
 // Warp-centric: every warp pulls whole bands from one global queue and keeps
@@ -145,8 +148,8 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
         if (lane == 0) u = (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(a.queue), 1ull);
         u = __shfl_sync(FULL, u, 0);
         if (u >= a.n_units) break;
-        int s, b;
-        unit_of(a, u, s, b);
+        int s, ub_lo, ub_hi;
+        unit_of(a, u, s, ub_lo, ub_hi, a.series);
         if (s != cur) {
             flush();
             cur = s;
@@ -170,6 +173,7 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
         if (bad) continue;
 
         const float *ys = a.y + sd.off;
+        for (int b = ub_lo; b < ub_hi; ++b) {
         int d_lo, d_hi;
         band_range(b, D, sd.ne, d_lo, d_hi);
         const int rows = sd.ne - d_lo;
@@ -220,6 +224,10 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
             for (int j = 0; j < D; ++j)
                 if (carry[j]) sink.emit(carry[j]);
         }
+        }  // bands of the unit
+        // flush after each unit: a warp's next unit is usually another series
+        flush();
+        cur = -1;
     }
     flush();
 }

@@ -65,10 +65,12 @@ struct CellArgs {
     const Item *items;
     int32_t n_items;
     int32_t band;
-    // warp-level work (line pass): every band of the series order[0..n_pos)
+    // warp-level work (line pass): units of `chunk` consecutive bands of the
+    // series order[0..n_pos)
     const int32_t *order;    // series, largest first
-    const int64_t *uprefix;  // n_pos + 1 prefix of band counts along order
+    const int64_t *uprefix;  // n_pos + 1 prefix of unit counts along order
     int32_t n_pos;
+    int32_t chunk;           // bands per unit
     int64_t n_units;
     unsigned int *queue;   // ticket counter (64-bit aligned), zeroed before launch
     int *status;
