@@ -28,6 +28,7 @@ struct LineSink {
     uint32_t *hs;           // this lane's row of the warp's shared histogram, index = length
     uint64_t *hist;         // this series' full histogram row for lane k, or null
     uint32_t lmax;
+    uint32_t c1, c2;        // interior lines of length 1 and 2, counted by popcount
     __device__ __forceinline__ void emit(uint32_t len)
     {
         if (len <= (uint32_t)LSH) {
@@ -37,40 +38,56 @@ struct LineSink {
         }
         lmax = max(lmax, len);
     }
+    // fold the popcount tallies into the histogram row
+    __device__ __forceinline__ void settle()
+    {
+        hs[1] += c1;
+        hs[2] += c2;
+        if (c2) lmax = max(lmax, 2u);
+        if (c1) lmax = max(lmax, 1u);
+        c1 = c2 = 0;
+    }
 };
 
 // Runs of one 32-cell word (bit t = row i0+t) joined with the open run c.
+// Branch-free for the common cases: the run open from the previous word is
+// extended by the word's low ones and closes at its first zero; the high ones
+// stay open.  Lines strictly inside the word are bounded by zeros: those of
+// length 1 and 2 are counted with popcounts of the run-start mask, longer
+// ones are read one by one with __ffs.
 template <class Sink>
 __device__ __forceinline__ void runs_word(uint32_t w, uint32_t &c, Sink &sink)
 {
-    if (w == 0u) {
-        if (c) {
-            sink.emit(c);
-            c = 0;
-        }
-        return;
-    }
-    if (w == FULL) {
-        c += 32;
-        return;
-    }
-    const uint32_t t0 = __ffs(~w) - 1;   // ones at the bottom: they extend the open run
+    const bool full = (w == FULL);
+    const uint32_t t0 = full ? 32u : (uint32_t)(__ffs(~w) - 1);  // low ones
     const uint32_t lead = c + t0;
-    if (lead) sink.emit(lead);           // ... which ends below the first zero
-    const uint32_t tl = __clz(~w);       // ones at the top: they stay open
-    uint32_t mid = w & (FULL << t0);
-    if (tl) mid &= (FULL >> tl);
-    while (mid) {                        // closed runs strictly inside the word
-        const uint32_t low = mid & (0u - mid);
-        const uint32_t nxt = mid + low;  // clears the lowest run
-        sink.emit(__popc(mid & ~nxt));
-        mid &= nxt;
+    if (!full && lead) sink.emit(lead);
+    const uint32_t tl = full ? 0u : (uint32_t)__clz(~w);         // high ones
+    const uint32_t mid = full ? 0u : (w & (FULL << t0) & (FULL >> tl));
+    if (mid) {
+        const uint32_t st = mid & ~(mid << 1);   // first cell of each interior line
+        const uint32_t a2 = mid & (mid >> 1);    // cell with its successor set
+        uint32_t x = st & a2 & (mid >> 2);       // starts of lines of length >= 3
+        const uint32_t n1 = __popc(st), n2 = __popc(st & a2), n3 = __popc(x);
+        sink.c1 += n1 - n2;
+        sink.c2 += n2 - n3;
+        while (x) {
+            const int p = __ffs(x) - 1;
+            sink.emit((uint32_t)(__ffs(~(mid >> p)) - 1));
+            x &= x - 1;
+        }
     }
-    c = tl;
+    c = full ? c + 32u : tl;
 }
 
-// Per-warp shared memory: the warp's own short-line histogram and thresholds.
-__host__ __device__ constexpr int warp_smem_words(int K) { return K * HS_STRIDE + 32; }
+// Rank table: keys bucketed by key >> shift, at most one distinct threshold
+// per bucket; entry = rank at the bucket start (bits 0-4), thresholds in the
+// bucket (bits 5-10) and their key's offset inside the bucket (bits 11-31).
+constexpr int TMAX = 512;
+
+// Per-warp shared memory: the warp's own short-line histogram, thresholds and
+// rank table.
+__host__ __device__ constexpr int warp_smem_words(int K) { return K * HS_STRIDE + 32 + TMAX; }
 
 int lines_smem_bytes(int K) { return WARPS * warp_smem_words(K) * 4; }
 
@@ -101,6 +118,7 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *hs = reinterpret_cast<uint32_t *>(smem) + warp * warp_smem_words(K);
     uint32_t *epsb = hs + K * HS_STRIDE;
+    uint32_t *tab = epsb + 32;
     const bool klane = lane < K;
 
     // lane k's bits as masks, for the bit-sliced test r <= k
@@ -119,10 +137,15 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
     sink.hs = hs + lane * HS_STRIDE;
     sink.hist = nullptr;
     sink.lmax = 0;
+    sink.c1 = sink.c2 = 0;
+    int tshift = 0, tbase = 0, tnb = 0;
+    uint32_t tmask = 0;
+    bool use_tab = false;
 
     auto flush = [&]() {
         if (cur < 0) return;
         if (klane) {
+            sink.settle();
             const int64_t o = (int64_t)cur * K + lane;
             if (cnt) atomicAdd(reinterpret_cast<unsigned long long *>(lb.count + o),
                                (unsigned long long)cnt);
@@ -166,6 +189,39 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
             bad = !__all_sync(FULL, ok);
             epsb[lane] = v;
             if (bad && lane == 0) set_status(a.status, 8 /*UNSORTED*/);
+            // rank table: the widest buckets that still separate every pair
+            // of distinct thresholds
+            tshift = 21;
+            for (; tshift > 0; --tshift) {
+                const bool clash = klane && lane > 0 && prev != v && (prev >> tshift) == (v >> tshift);
+                if (!__any_sync(FULL, clash)) break;
+            }
+            const uint32_t vmin = __shfl_sync(FULL, v, 0), vmax = __shfl_sync(FULL, v, K - 1);
+            tbase = (int)(vmin >> tshift);
+            tnb = (int)(vmax >> tshift) - tbase + 1;
+            tmask = (1u << tshift) - 1u;
+            use_tab = !bad && tnb + 2 <= TMAX;
+            __syncwarp();
+            if (use_tab) {
+                for (int q = lane; q < tnb + 2; q += 32) {
+                    uint32_t e;
+                    if (q == 0) {
+                        e = 0u;                    // below every threshold's bucket
+                    } else if (q == tnb + 1) {
+                        e = (uint32_t)K;           // above: all K thresholds are smaller
+                    } else {
+                        uint32_t rlo = 0, cnt = 0, off = 0;
+                        for (int k = 0; k < K; ++k) {
+                            const uint32_t ek = epsb[k];
+                            const int eb = (int)(ek >> tshift) - tbase;
+                            if (eb < q - 1) ++rlo;
+                            else if (eb == q - 1) { ++cnt; off = ek & tmask; }
+                        }
+                        e = rlo | (cnt << 5) | (off << 11);
+                    }
+                    tab[q] = e;
+                }
+            }
             if (HIST && klane)
                 sink.hist = lb.hist + lb.hist_off[s] + (int64_t)lane * (sd.ne - 1);
             __syncwarp();
@@ -190,12 +246,18 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
                 uint32_t r = 31;  // outside the diagonal: recurrent for no k
                 if (i < sd.ne - dl) {
                     const uint32_t key = __float_as_uint(tile.dist(ys, j, i, dl, sd.tau, sd.m));
-                    r = 0;
-                    r += (epsb[r + 15] < key) ? 16u : 0u;
-                    r += (epsb[r + 7] < key) ? 8u : 0u;
-                    r += (epsb[r + 3] < key) ? 4u : 0u;
-                    r += (epsb[r + 1] < key) ? 2u : 0u;
-                    r += (epsb[r] < key) ? 1u : 0u;
+                    if (use_tab) {
+                        const int q = min(max((int)(key >> tshift) - tbase, -1), tnb) + 1;
+                        const uint32_t e = tab[q];
+                        r = (e & 31u) + (((key & tmask) > (e >> 11)) ? ((e >> 5) & 63u) : 0u);
+                    } else {
+                        r = 0;
+                        r += (epsb[r + 15] < key) ? 16u : 0u;
+                        r += (epsb[r + 7] < key) ? 8u : 0u;
+                        r += (epsb[r + 3] < key) ? 4u : 0u;
+                        r += (epsb[r + 1] < key) ? 2u : 0u;
+                        r += (epsb[r] < key) ? 1u : 0u;
+                    }
                 }
                 const uint32_t B0 = __ballot_sync(FULL, r & 1u);
                 const uint32_t B1 = __ballot_sync(FULL, r & 2u);
