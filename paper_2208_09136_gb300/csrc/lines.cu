@@ -28,14 +28,14 @@ struct LineSink {
     uint32_t *hs;           // this lane's row of the warp's shared histogram, index = length
     uint64_t *hist;         // this series' full histogram row for lane k, or null
     uint32_t lmax;
-    uint32_t c1, c2;        // interior lines of length 1 and 2, counted by popcount
+    uint32_t c1, c2, c3;    // interior lines of length 1, 2, 3, counted by popcount
+    bool real;              // lane < K (the other lanes write a dummy row)
+    // one line of length len; len == 0 means none (slot 0 is a scratch slot)
     __device__ __forceinline__ void emit(uint32_t len)
     {
-        if (len <= (uint32_t)LSH) {
-            hs[len] += 1u;  // the row belongs to this lane alone
-        } else if (HIST) {
+        hs[len <= (uint32_t)LSH ? len : 0u] += 1u;  // the row belongs to this lane alone
+        if (HIST && len > (uint32_t)LSH && real)
             atomicAdd(reinterpret_cast<unsigned long long *>(hist + (len - 1)), 1ull);
-        }
         lmax = max(lmax, len);
     }
     // fold the popcount tallies into the histogram row
@@ -43,39 +43,39 @@ struct LineSink {
     {
         hs[1] += c1;
         hs[2] += c2;
-        if (c2) lmax = max(lmax, 2u);
-        if (c1) lmax = max(lmax, 1u);
-        c1 = c2 = 0;
+        hs[3] += c3;
+        lmax = max(lmax, c3 ? 3u : c2 ? 2u : c1 ? 1u : 0u);
+        c1 = c2 = c3 = 0;
     }
 };
 
-// Runs of one 32-cell word (bit t = row i0+t) joined with the open run c.
-// Branch-free for the common cases: the run open from the previous word is
-// extended by the word's low ones and closes at its first zero; the high ones
-// stay open.  Lines strictly inside the word are bounded by zeros: those of
-// length 1 and 2 are counted with popcounts of the run-start mask, longer
-// ones are read one by one with __ffs.
+// Runs of one 32-cell word (bit t = row i0+t) joined with the open run c,
+// without branches on the word's content: the run open from the previous
+// word is extended by the word's low ones and closes at its first zero; the
+// high ones stay open.  Lines strictly inside the word are bounded by zeros:
+// those of length 1..3 are counted with popcounts of the run-start mask,
+// longer ones are read one by one with __ffs.
 template <class Sink>
 __device__ __forceinline__ void runs_word(uint32_t w, uint32_t &c, Sink &sink)
 {
     const bool full = (w == FULL);
-    const uint32_t t0 = full ? 32u : (uint32_t)(__ffs(~w) - 1);  // low ones
-    const uint32_t lead = c + t0;
-    if (!full && lead) sink.emit(lead);
-    const uint32_t tl = full ? 0u : (uint32_t)__clz(~w);         // high ones
+    const uint32_t nw = ~w;
+    const uint32_t t0 = full ? 0u : (uint32_t)(__ffs(nw) - 1);  // low ones
+    const uint32_t tl = full ? 0u : (uint32_t)__clz(nw);        // high ones
+    sink.emit(full ? 0u : c + t0);
     const uint32_t mid = full ? 0u : (w & (FULL << t0) & (FULL >> tl));
-    if (mid) {
-        const uint32_t st = mid & ~(mid << 1);   // first cell of each interior line
-        const uint32_t a2 = mid & (mid >> 1);    // cell with its successor set
-        uint32_t x = st & a2 & (mid >> 2);       // starts of lines of length >= 3
-        const uint32_t n1 = __popc(st), n2 = __popc(st & a2), n3 = __popc(x);
-        sink.c1 += n1 - n2;
-        sink.c2 += n2 - n3;
-        while (x) {
-            const int p = __ffs(x) - 1;
-            sink.emit((uint32_t)(__ffs(~(mid >> p)) - 1));
-            x &= x - 1;
-        }
+    const uint32_t st = mid & ~(mid << 1);   // first cell of each interior line
+    const uint32_t s2 = st & (mid >> 1);     // ... of lines of length >= 2
+    const uint32_t s3 = s2 & (mid >> 2);     // >= 3
+    uint32_t x = s3 & (mid >> 3);            // >= 4
+    const uint32_t n1 = __popc(st), n2 = __popc(s2), n3 = __popc(s3);
+    sink.c1 += n1 - n2;
+    sink.c2 += n2 - n3;
+    sink.c3 += n3 - __popc(x);
+    while (x) {
+        const int p = __ffs(x) - 1;
+        sink.emit((uint32_t)(__ffs(~(mid >> p)) - 1));
+        x &= x - 1;
     }
     c = full ? c + 32u : tl;
 }
@@ -85,9 +85,9 @@ __device__ __forceinline__ void runs_word(uint32_t w, uint32_t &c, Sink &sink)
 // bucket (bits 5-10) and their key's offset inside the bucket (bits 11-31).
 constexpr int TMAX = 512;
 
-// Per-warp shared memory: the warp's own short-line histogram, thresholds and
-// rank table.
-__host__ __device__ constexpr int warp_smem_words(int K) { return K * HS_STRIDE + 32 + TMAX; }
+// Per-warp shared memory: the warp's own short-line histogram (K rows plus a
+// scratch row for lanes >= K), thresholds and rank table.
+__host__ __device__ constexpr int warp_smem_words(int K) { return (K + 1) * HS_STRIDE + 32 + TMAX; }
 
 int lines_smem_bytes(int K) { return WARPS * warp_smem_words(K) * 4; }
 
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *hs = reinterpret_cast<uint32_t *>(smem) + warp * warp_smem_words(K);
-    uint32_t *epsb = hs + K * HS_STRIDE;
+    uint32_t *epsb = hs + (K + 1) * HS_STRIDE;
     uint32_t *tab = epsb + 32;
     const bool klane = lane < K;
 
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
 #pragma unroll
     for (int b = 0; b < 5; ++b) km[b] = ((lane >> b) & 1) ? FULL : 0u;
 
-    for (int x = lane; x < K * HS_STRIDE; x += 32) hs[x] = 0;
+    for (int x = lane; x < (K + 1) * HS_STRIDE; x += 32) hs[x] = 0;
     __syncwarp();
 
     int cur = -1;
@@ -134,10 +134,11 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
     SeriesDev sd{};
     uint64_t cnt = 0;
     LineSink<HIST> sink;
-    sink.hs = hs + lane * HS_STRIDE;
+    sink.hs = hs + min(lane, K) * HS_STRIDE;
     sink.hist = nullptr;
     sink.lmax = 0;
-    sink.c1 = sink.c2 = 0;
+    sink.c1 = sink.c2 = sink.c3 = 0;
+    sink.real = klane;
     int tshift = 0, tbase = 0, tnb = 0;
     uint32_t tmask = 0;
     bool use_tab = false;
@@ -153,6 +154,7 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
         }
         cnt = 0;
         sink.lmax = 0;
+        sink.c1 = sink.c2 = sink.c3 = 0;
         __syncwarp();
         uint64_t *gs = lb.hshort + (int64_t)cur * K * LSH;
         for (int x = lane; x < K * LSH; x += 32) {
@@ -264,28 +266,25 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
                 const uint32_t B2 = __ballot_sync(FULL, r & 4u);
                 const uint32_t B3 = __ballot_sync(FULL, r & 8u);
                 const uint32_t B4 = __ballot_sync(FULL, r & 16u);
-                if (klane) {
-                    // gt = {t : r_t > k}, most significant bit plane first
-                    uint32_t gt = B4 & ~km[4];
-                    uint32_t eq = ~(B4 ^ km[4]);
-                    gt |= eq & B3 & ~km[3];
-                    eq &= ~(B3 ^ km[3]);
-                    gt |= eq & B2 & ~km[2];
-                    eq &= ~(B2 ^ km[2]);
-                    gt |= eq & B1 & ~km[1];
-                    eq &= ~(B1 ^ km[1]);
-                    gt |= eq & B0 & ~km[0];
-                    const uint32_t w = ~gt;
-                    cnt += __popc(w);
-                    runs_word(w, carry[j], sink);
-                }
+                // lane k's word {t : r_t <= k}; gt = {t : r_t > k}, most
+                // significant bit plane first.  Lanes >= K run the same code
+                // on their scratch row, so the warp never diverges here.
+                uint32_t gt = B4 & ~km[4];
+                uint32_t eq = ~(B4 ^ km[4]);
+                gt |= eq & B3 & ~km[3];
+                eq &= ~(B3 ^ km[3]);
+                gt |= eq & B2 & ~km[2];
+                eq &= ~(B2 ^ km[2]);
+                gt |= eq & B1 & ~km[1];
+                eq &= ~(B1 ^ km[1]);
+                gt |= eq & B0 & ~km[0];
+                const uint32_t w = ~gt;
+                cnt += __popc(w);
+                runs_word(w, carry[j], sink);
             }
         }
-        if (klane) {
 #pragma unroll
-            for (int j = 0; j < D; ++j)
-                if (carry[j]) sink.emit(carry[j]);
-        }
+        for (int j = 0; j < D; ++j) sink.emit(carry[j]);  // lines reaching the diagonal's end
         }  // bands of the unit
         // flush after each unit: a warp's next unit is usually another series
         flush();
