@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-cells", type=float, default=1.2e8,
                     help="cells of the oracle's bounded sample")
+    ap.add_argument("--band", type=int, default=0, help="line-pass band width (0 = default)")
     return ap.parse_args()
 
 
@@ -269,7 +270,8 @@ def main():
     stream.synchronize()
 
     def make_ctx(schedule):
-        return rqa.Context(device=dev, stream=stream, schedule=schedule, select=rqa.RQA_SELECT_RADIX)
+        return rqa.Context(device=dev, stream=stream, schedule=schedule, select=rqa.RQA_SELECT_RADIX,
+                           band=args.band)
 
     def step(ctx, yb=None):
         b = batch if yb is None else yb
@@ -421,6 +423,7 @@ def main():
             "config": {"workload": args.workload, "desc": workload_desc(args.workload),
                        "form": f"{form} + radix select" if not have_model else f"{form} + learned bracket",
                        "series": S, "cells_per_step": total_cells, "l2": "flushed between steps",
+                       "line_band": rqa.rqa_device_info(ctx)["band"],
                        "parallelism": f"replicas x{world} (series-independent)"},
             "series_per_s": series_per_s,
             "phase_ms": {n: round(float(v), 4) for n, v in zip(names, phase)},

@@ -84,7 +84,9 @@ typedef struct {
     void *stream;      /* cudaStream_t owned by the caller; NULL = default stream */
     int schedule;      /* RQA_SCHED_* */
     int select;        /* RQA_SELECT_* */
-    int band;          /* diagonals per warp band: 0 = tuned default, else 8/16/32 */
+    int band;          /* diagonals per warp band of the line pass: 0 = default
+                          (8), else 4, 8 or 16 (4 and 16 only for (m, tau) =
+                          (1, any), (3, 1), (3, 3); otherwise 8 is used) */
     int blocks_per_sm; /* persistent CTAs per SM: 0 = tuned default */
     int reserved[4];   /* must be zero */
 } rqa_config;
@@ -174,7 +176,7 @@ typedef struct {
  *              does
  *   rr_num     host, K numerators (read only when eps == NULL)
  *   lmin       host, n_lmin (1..RQA_LMIN_MAX) minimal line lengths, each in
- *              1..129 (paper: 2); DET_k(lmin) is NaN when C_k = 0
+ *              1..65 (paper: 2); DET_k(lmin) is NaN when C_k = 0
  *   det_out    device, S*K*n_lmin FP64, [s][k][j] = DET_k(lmin[j]) (may be NULL)
  *   det_avg    device, S*n_lmin FP64, [s][j] = (1/K) sum_k DET_k(lmin[j])
  *   eps_used   device, S*K FP32 copy of the thresholds used (may be NULL)

@@ -46,7 +46,8 @@ struct rqa_ctx {
     cudaStream_t stream = nullptr;
     int schedule = RQA_SCHED_BATCHED;
     int select = RQA_SELECT_AUTO;
-    int band = 16;
+    int band = 16;          // diagonals per band of the counting rounds
+    int band_lines = 0;     // ... of the line pass (0 = tuned default)
     int bpsm = 0;
     int sm_count = 0;
 
@@ -84,6 +85,7 @@ struct Plan {
     std::vector<int32_t> order;              // series by size, largest first
     std::vector<int64_t> uprefix;            // S+1 unit-count prefix along order
     int32_t chunk = 1;                       // bands per line-pass unit (batched)
+    int32_t band_lines = DL_DEFAULT;         // diagonals per band of the line pass
     std::vector<int32_t> ident;              // 0..S-1
     std::vector<int64_t> uprefix1;           // [2s], [2s+1] = 0, units of s alone
     std::vector<int32_t> chunk1;             // bands per unit of s alone
@@ -249,8 +251,11 @@ int make_plan(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_
     auto chunk_for = [&](int64_t bands) {
         return (int32_t)std::max<int64_t>(4, std::min<int64_t>(64, bands / (n_warps * 8)));
     };
+    pl.band_lines = c->band_lines ? c->band_lines : DL_DEFAULT;
+    if (!lines_band_ok(pl.mt, pl.band_lines)) pl.band_lines = DL_DEFAULT;
+    auto nbl = [&](int s) { return (int64_t)(pl.sd[s].ne - 1 + pl.band_lines - 1) / pl.band_lines; };
     int64_t total_bands = 0;
-    for (int s = 0; s < S; ++s) total_bands += pl.sd[s].nbands;
+    for (int s = 0; s < S; ++s) total_bands += nbl(s);
     pl.chunk = chunk_for(total_bands);
     pl.order.resize(S);
     for (int s = 0; s < S; ++s) pl.order[s] = s;
@@ -258,15 +263,15 @@ int make_plan(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_
                      [&](int x, int y) { return pl.sd[x].P > pl.sd[y].P; });
     pl.uprefix.assign(S + 1, 0);
     for (int i = 0; i < S; ++i)
-        pl.uprefix[i + 1] = pl.uprefix[i] + (pl.sd[pl.order[i]].nbands + pl.chunk - 1) / pl.chunk;
+        pl.uprefix[i + 1] = pl.uprefix[i] + (nbl(pl.order[i]) + pl.chunk - 1) / pl.chunk;
     pl.ident.resize(S);
     pl.uprefix1.resize(2 * (size_t)S);
     pl.chunk1.resize(S);
     for (int s = 0; s < S; ++s) {
         pl.ident[s] = s;
-        pl.chunk1[s] = chunk_for(pl.sd[s].nbands);
+        pl.chunk1[s] = chunk_for(nbl(s));
         pl.uprefix1[2 * s] = 0;
-        pl.uprefix1[2 * s + 1] = (pl.sd[s].nbands + pl.chunk1[s] - 1) / pl.chunk1[s];
+        pl.uprefix1[2 * s + 1] = (nbl(s) + pl.chunk1[s] - 1) / pl.chunk1[s];
     }
     return RQA_OK;
 }
@@ -464,6 +469,7 @@ int run_lines(rqa_ctx *c, const Plan &pl, const float *eps, uint64_t *hist, cons
     a.y = pl.y;
     a.series = pl.d_sd;
     a.band = c->band;
+    a.band_lines = pl.band_lines;
     a.status = P<int>(c->status);
     unsigned *q = nullptr;
     const int full_grid = persistent_grid(c, (size_t)1 << 30);
@@ -588,7 +594,8 @@ int rqa_create(rqa_ctx **out, const rqa_config *cfg)
     if (cfg->schedule != RQA_SCHED_BATCHED && cfg->schedule != RQA_SCHED_PER_SERIES)
         return RQA_ERR_INVALID_ARG;
     if (cfg->select < RQA_SELECT_AUTO || cfg->select > RQA_SELECT_BRACKET) return RQA_ERR_INVALID_ARG;
-    if (cfg->band != 0 && cfg->band != 16) return RQA_ERR_INVALID_ARG;
+    if (cfg->band != 0 && cfg->band != 4 && cfg->band != 8 && cfg->band != 16)
+        return RQA_ERR_INVALID_ARG;
     if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 8) return RQA_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
@@ -602,7 +609,8 @@ int rqa_create(rqa_ctx **out, const rqa_config *cfg)
     c->stream = static_cast<cudaStream_t>(cfg->stream);
     c->schedule = cfg->schedule;
     c->select = cfg->select;
-    c->band = cfg->band ? cfg->band : 16;
+    c->band = BAND;
+    c->band_lines = cfg->band;
     c->bpsm = cfg->blocks_per_sm;
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess ||
@@ -656,7 +664,7 @@ int rqa_device_info(rqa_ctx *c, int *sm_count, int *band, int *blocks_per_sm)
 {
     if (!c) return RQA_ERR_INVALID_ARG;
     if (sm_count) *sm_count = c->sm_count;
-    if (band) *band = c->band;
+    if (band) *band = c->band_lines ? c->band_lines : DL_DEFAULT;
     if (blocks_per_sm) *blocks_per_sm = c->bpsm > 0 ? c->bpsm : 2;
     return RQA_OK;
 }

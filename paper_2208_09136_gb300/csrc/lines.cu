@@ -21,11 +21,10 @@
 
 namespace rqa {
 
-constexpr int HS_STRIDE = LSH + 1;  // +1: spreads lanes of one length over banks
 
 template <bool HIST>
 struct LineSink {
-    uint32_t *hs;           // this lane's row of the warp's shared histogram, index = length
+    uint32_t *hs;           // this lane's column of the warp's shared histogram, [length][lane]
     uint64_t *hist;         // this series' full histogram row for lane k, or null
     uint32_t lmax;
     uint32_t c1, c2, c3;    // interior lines of length 1, 2, 3, counted by popcount
@@ -33,7 +32,7 @@ struct LineSink {
     // one line of length len; len == 0 means none (slot 0 is a scratch slot)
     __device__ __forceinline__ void emit(uint32_t len)
     {
-        hs[len <= (uint32_t)LSH ? len : 0u] += 1u;  // the row belongs to this lane alone
+        hs[(len <= (uint32_t)LSH ? len : 0u) * 32u] += 1u;  // own column: own bank
         if (HIST && len > (uint32_t)LSH && real)
             atomicAdd(reinterpret_cast<unsigned long long *>(hist + (len - 1)), 1ull);
         lmax = max(lmax, len);
@@ -41,9 +40,9 @@ struct LineSink {
     // fold the popcount tallies into the histogram row
     __device__ __forceinline__ void settle()
     {
-        hs[1] += c1;
-        hs[2] += c2;
-        hs[3] += c3;
+        hs[1 * 32] += c1;
+        hs[2 * 32] += c2;
+        hs[3 * 32] += c3;
         lmax = max(lmax, c3 ? 3u : c2 ? 2u : c1 ? 1u : 0u);
         c1 = c2 = c3 = 0;
     }
@@ -85,11 +84,12 @@ __device__ __forceinline__ void runs_word(uint32_t w, uint32_t &c, Sink &sink)
 // bucket (bits 5-10) and their key's offset inside the bucket (bits 11-31).
 constexpr int TMAX = 512;
 
-// Per-warp shared memory: the warp's own short-line histogram (K rows plus a
-// scratch row for lanes >= K), thresholds and rank table.
-__host__ __device__ constexpr int warp_smem_words(int K) { return (K + 1) * HS_STRIDE + 32 + TMAX; }
+// Per-warp shared memory: the warp's own short-line histogram laid out
+// [length 0..LSH][lane] (each lane owns one bank; length 0 is a scratch slot,
+// lanes >= K own scratch columns), thresholds and rank table.
+__host__ __device__ constexpr int warp_smem_words() { return (LSH + 1) * 32 + 32 + TMAX; }
 
-int lines_smem_bytes(int K) { return WARPS * warp_smem_words(K) * 4; }
+int lines_smem_bytes(int) { return WARPS * warp_smem_words() * 4; }
 
 // Series s and bands [b_lo, b_hi) of work unit u: a unit is a.chunk
 // consecutive bands of one series; units run over the series in a.order
@@ -105,7 +105,7 @@ __device__ __forceinline__ void unit_of(const CellArgs &a, int64_t u, int &s, in
     }
     s = a.order[lo];
     b_lo = (int)(u - a.uprefix[lo]) * a.chunk;
-    b_hi = min(b_lo + a.chunk, series[s].nbands);
+    b_hi = min(b_lo + a.chunk, (series[s].ne - 1 + a.band_lines - 1) / a.band_lines);
 }
 
 // Warp-centric: every warp pulls whole bands from one global queue and keeps
@@ -116,8 +116,8 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *hs = reinterpret_cast<uint32_t *>(smem) + warp * warp_smem_words(K);
-    uint32_t *epsb = hs + (K + 1) * HS_STRIDE;
+    uint32_t *hs = reinterpret_cast<uint32_t *>(smem) + warp * warp_smem_words();
+    uint32_t *epsb = hs + (LSH + 1) * 32;
     uint32_t *tab = epsb + 32;
     const bool klane = lane < K;
 
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
 #pragma unroll
     for (int b = 0; b < 5; ++b) km[b] = ((lane >> b) & 1) ? FULL : 0u;
 
-    for (int x = lane; x < (K + 1) * HS_STRIDE; x += 32) hs[x] = 0;
+    for (int x = lane; x < (LSH + 1) * 32; x += 32) hs[x] = 0;
     __syncwarp();
 
     int cur = -1;
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
     SeriesDev sd{};
     uint64_t cnt = 0;
     LineSink<HIST> sink;
-    sink.hs = hs + min(lane, K) * HS_STRIDE;
+    sink.hs = hs + lane;
     sink.hist = nullptr;
     sink.lmax = 0;
     sink.c1 = sink.c2 = sink.c3 = 0;
@@ -156,13 +156,13 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
         sink.lmax = 0;
         sink.c1 = sink.c2 = sink.c3 = 0;
         __syncwarp();
-        uint64_t *gs = lb.hshort + (int64_t)cur * K * LSH;
-        for (int x = lane; x < K * LSH; x += 32) {
-            const int k = x / LSH, l = x - k * LSH + 1;
-            const uint32_t v = hs[k * HS_STRIDE + l];
-            if (v) {
-                atomicAdd(reinterpret_cast<unsigned long long *>(gs + x), (unsigned long long)v);
-                hs[k * HS_STRIDE + l] = 0;
+        uint64_t *gs = lb.hshort + ((int64_t)cur * K + lane) * LSH;
+#pragma unroll 1
+        for (int l = 1; l <= LSH; ++l) {  // row l: one bank per lane
+            const uint32_t v = hs[l * 32 + lane];
+            if (klane && v) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(gs + (l - 1)), (unsigned long long)v);
+                hs[l * 32 + lane] = 0;
             }
         }
         __syncwarp();
@@ -293,20 +293,36 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
     flush();
 }
 
+template <int D, bool HIST>
+static void (*lines_kernel_d(int embed))(CellArgs, LineBufs, int)
+{
+    switch (embed) {
+    case E_M1T1: return k_lines<D, 1, 1, HIST>;
+    case E_M3T1: return k_lines<D, 3, 1, HIST>;
+    case E_M3T3: return k_lines<D, 3, 3, HIST>;
+    default: return nullptr;
+    }
+}
+
 template <bool HIST>
 static cudaError_t launch_lines_h(const CellArgs &a, const LineBufs &lb, int K, int grid,
-                                 int embed, cudaStream_t st)
+                                  int embed, cudaStream_t st)
 {
-    void (*kern)(CellArgs, LineBufs, int);
-    switch (embed) {
-    case E_M1T1: kern = k_lines<BAND, 1, 1, HIST>; break;
-    case E_M3T1: kern = k_lines<BAND, 3, 1, HIST>; break;
-    case E_M3T3: kern = k_lines<BAND, 3, 3, HIST>; break;
-    case E_M1: kern = k_lines<BAND, 1, 0, HIST>; break;
-    case E_M2: kern = k_lines<BAND, 2, 0, HIST>; break;
-    case E_M3: kern = k_lines<BAND, 3, 0, HIST>; break;
-    case E_M4: kern = k_lines<BAND, 4, 0, HIST>; break;
-    default: kern = k_lines<BAND, 0, 0, HIST>; break;
+    void (*kern)(CellArgs, LineBufs, int) = nullptr;
+    switch (a.band_lines) {  // band width: specialised embeddings only, others use 8
+    case 4: kern = lines_kernel_d<4, HIST>(embed); break;
+    case 16: kern = lines_kernel_d<16, HIST>(embed); break;
+    default: kern = lines_kernel_d<8, HIST>(embed); break;
+    }
+    if (!kern) {
+        if (a.band_lines != DL_DEFAULT) return cudaErrorInvalidValue;
+        switch (embed) {
+        case E_M1: kern = k_lines<DL_DEFAULT, 1, 0, HIST>; break;
+        case E_M2: kern = k_lines<DL_DEFAULT, 2, 0, HIST>; break;
+        case E_M3: kern = k_lines<DL_DEFAULT, 3, 0, HIST>; break;
+        case E_M4: kern = k_lines<DL_DEFAULT, 4, 0, HIST>; break;
+        default: kern = k_lines<DL_DEFAULT, 0, 0, HIST>; break;
+        }
     }
     const int smem = lines_smem_bytes(K);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -315,11 +331,19 @@ static cudaError_t launch_lines_h(const CellArgs &a, const LineBufs &lb, int K, 
     return cudaGetLastError();
 }
 
+// Band widths the line pass supports for an embedding variant.
+bool lines_band_ok(int embed, int band)
+{
+    if (band == DL_DEFAULT) return true;
+    const bool special = embed == E_M1T1 || embed == E_M3T1 || embed == E_M3T3;
+    return special && (band == 4 || band == 16);
+}
+
 cudaError_t launch_lines(const CellArgs &a, const LineBufs &lb, int K, int grid, int embed,
                          cudaStream_t st)
 {
     const bool hist = lb.hist != nullptr;
-    if (a.band != BAND) return cudaErrorInvalidValue;
+    if (!lines_band_ok(embed, a.band_lines)) return cudaErrorInvalidValue;
     if (!a.y || !a.series || !a.order || !a.uprefix || !a.queue || !a.status || !lb.eps ||
         !lb.count || !lb.lmax || !lb.hshort || (hist && !lb.hist_off) || K < 1 || K > KMAX ||
         grid < 1 || a.n_units < 1 || a.n_pos < 1)

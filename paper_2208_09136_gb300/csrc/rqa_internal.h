@@ -14,10 +14,11 @@ constexpr int COARSE_SHIFT = 20;
 constexpr int NCOARSE = 1 << 11;   // 2048 coarse buckets
 constexpr int NFINE = 1 << 10;     // 1024 bins per middle / low digit group
 constexpr int NSUB_MAX = 24;       // bracket-subdivided coarse buckets per series
-constexpr int LSH = 128;           // line lengths 1..LSH counted in shared memory
+constexpr int LSH = 64;            // line lengths 1..LSH counted in shared memory
 constexpr int LMIN_MAX = 8;        // entries of an lmin list
 constexpr int THREADS = 256;       // threads per CTA of the cell kernels
-constexpr int BAND = 16;           // diagonals per warp band
+constexpr int BAND = 16;           // diagonals per warp band of the counting rounds
+constexpr int DL_DEFAULT = 8;      // diagonals per warp band of the line pass
 constexpr int WARPS = THREADS / 32;
 
 // Counting rounds of the selection.
@@ -71,6 +72,7 @@ struct CellArgs {
     const int64_t *uprefix;  // n_pos + 1 prefix of unit counts along order
     int32_t n_pos;
     int32_t chunk;           // bands per unit
+    int32_t band_lines;      // diagonals per band of the line pass (4, 8 or 16)
     int64_t n_units;
     unsigned int *queue;   // ticket counter (64-bit aligned), zeroed before launch
     int *status;
@@ -95,6 +97,7 @@ struct LineBufs {
 };
 cudaError_t launch_lines(const CellArgs &a, const LineBufs &lb, int K, int grid, int embed,
                          cudaStream_t st);
+bool lines_band_ok(int embed, int band);
 cudaError_t launch_finalize_det(const LineBufs &lb, const SeriesDev *series, int S, int K,
                                 const int32_t *lmin_dev, int n_lmin, double *det,
                                 double *det_avg, cudaStream_t st);
