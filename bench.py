@@ -250,7 +250,8 @@ def main():
     total_cells = int(cells.sum())
     S, K = len(offsets) - 1, len(RR)
     form = args.form
-    have_model = False
+    from paper_2208_09136_gb300 import bracket
+    have_model = os.path.exists(bracket.MODEL_PATH) and form != "plain"
     if form == "auto":
         form = "batched"
     stream = torch.cuda.Stream(device=dev)
@@ -269,9 +270,13 @@ def main():
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream.synchronize()
 
-    def make_ctx(schedule):
-        return rqa.Context(device=dev, stream=stream, schedule=schedule, select=rqa.RQA_SELECT_RADIX,
-                           band=args.band)
+    def make_ctx(schedule, learned=False):
+        c = rqa.Context(device=dev, stream=stream, schedule=schedule,
+                        select=rqa.RQA_SELECT_BRACKET if learned else rqa.RQA_SELECT_RADIX,
+                        band=args.band)
+        if learned:
+            bracket.install(c)
+        return c
 
     def step(ctx, yb=None):
         b = batch if yb is None else yb
@@ -282,7 +287,7 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    ctx = make_ctx(sched)
+    ctx = make_ctx(sched, have_model)
     rqa.rqa_set_timing(ctx, True)
     for _ in range(args.warmup):
         step(ctx)
@@ -309,6 +314,7 @@ def main():
     barrier()
     clk = clocks.stop()
     launches = rqa.rqa_kernel_launches(ctx) - launches0
+    bstats = rqa.rqa_bracket_stats(ctx) if have_model else None
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     code = rqa.rqa_status(ctx)
     if code:
@@ -428,6 +434,8 @@ def main():
             "series_per_s": series_per_s,
             "phase_ms": {n: round(float(v), 4) for n, v in zip(names, phase)},
             "gpu_launches": int(launches),
+            "bracket": None if bstats is None else {"hits": bstats[0], "misses": bstats[1],
+                                                    "miss_rate": bstats[1] / max(1, sum(bstats))},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -26,6 +26,10 @@ RQA_SELECT_AUTO, RQA_SELECT_RADIX, RQA_SELECT_BRACKET = 0, 1, 2
 RQA_K_MAX = 31
 RQA_LMIN_MAX = 8
 RQA_FEATURES = 131
+RQA_MLP_HIDDEN = 256
+RQA_MLP_OUT = 40
+RQA_MLP_PARAMS = 256 * 131 + 256 + 256 * 256 + 256 + 40 * 256 + 40
+RQA_MLP_ACTS = 512
 
 
 class RqaError(RuntimeError):
@@ -66,6 +70,14 @@ _SIGS = {
     "rqa_kernel_launches": ([c_vp], c_u64),
     "rqa_line_hist": ([c_vp, ctypes.POINTER(_Batch), c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp],
                       c_int),
+    "rqa_sketch": ([c_vp, ctypes.POINTER(_Batch), c_u64, c_vp, c_vp, c_vp], c_int),
+    "rqa_mlp_forward": ([c_vp, c_vp, c_vp, c_i32, c_vp, c_vp], c_int),
+    "rqa_mlp_backward": ([c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_i32, ctypes.c_float, ctypes.c_float,
+                          c_vp, c_vp], c_int),
+    "rqa_adam_step": ([c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, c_i32, ctypes.c_float, ctypes.c_float,
+                       ctypes.c_float, ctypes.c_float], c_int),
+    "rqa_set_bracket_model": ([c_vp, c_vp, ctypes.c_float], c_int),
+    "rqa_bracket_stats": ([c_vp, c_vp, c_vp], c_int),
 }
 
 
@@ -290,3 +302,62 @@ def rqa_line_hist(ctx: Context, batch: Batch, eps, K: int, hist=None, hist_offse
                                _np_ptr(hoff), _dev_ptr(lmax, torch.uint32, S * K, "lmax"),
                                _dev_ptr(count, torch.uint64, S * K, "count"),
                                _dev_ptr(stencil, torch.uint64, S * K, "stencil")), "rqa_line_hist")
+
+
+# ------------------------------------------------------------ learned bracket
+def rqa_sketch(ctx: Context, batch: Batch, seed: int, feats, centre=None, qdist=None):
+    import torch
+    S = batch.n_series
+    b = batch._c()
+    _check(lib().rqa_sketch(ctx.handle, ctypes.byref(b), int(seed) & ((1 << 64) - 1),
+                            _dev_ptr(feats, torch.float32, S * RQA_FEATURES, "feats"),
+                            _dev_ptr(centre, torch.float32, S, "centre"),
+                            _dev_ptr(qdist, torch.float32, S * 128, "qdist")), "rqa_sketch")
+
+
+def rqa_mlp_forward(ctx: Context, params, X, Y, acts=None):
+    import torch
+    B = X.shape[0]
+    _check(lib().rqa_mlp_forward(ctx.handle, _dev_ptr(params, torch.float32, RQA_MLP_PARAMS, "params"),
+                                 _dev_ptr(X, torch.float32, B * RQA_FEATURES, "X"), int(B),
+                                 _dev_ptr(Y, torch.float32, B * RQA_MLP_OUT, "Y"),
+                                 _dev_ptr(acts, torch.float32, B * RQA_MLP_ACTS, "acts")),
+           "rqa_mlp_forward")
+
+
+def rqa_mlp_backward(ctx: Context, params, X, acts, Y, T, tau_lo: float, tau_hi: float, grads,
+                     loss=None):
+    import torch
+    B = X.shape[0]
+    _check(lib().rqa_mlp_backward(ctx.handle, _dev_ptr(params, torch.float32, RQA_MLP_PARAMS, "params"),
+                                  _dev_ptr(X, torch.float32, B * RQA_FEATURES, "X"),
+                                  _dev_ptr(acts, torch.float32, B * RQA_MLP_ACTS, "acts"),
+                                  _dev_ptr(Y, torch.float32, B * RQA_MLP_OUT, "Y"),
+                                  _dev_ptr(T, torch.float32, B * (RQA_MLP_OUT // 2), "T"), int(B),
+                                  float(tau_lo), float(tau_hi),
+                                  _dev_ptr(grads, torch.float32, RQA_MLP_PARAMS, "grads"),
+                                  _dev_ptr(loss, torch.float32, 1, "loss")), "rqa_mlp_backward")
+
+
+def rqa_adam_step(ctx: Context, params, grads, m, v, t: int, lr: float, beta1: float = 0.9,
+                  beta2: float = 0.999, eps: float = 1e-8):
+    import torch
+    n = params.numel()
+    _check(lib().rqa_adam_step(ctx.handle, _dev_ptr(params, torch.float32, n, "params"),
+                               _dev_ptr(grads, torch.float32, n, "grads"),
+                               _dev_ptr(m, torch.float32, n, "m"), _dev_ptr(v, torch.float32, n, "v"),
+                               int(n), int(t), float(lr), float(beta1), float(beta2), float(eps)),
+           "rqa_adam_step")
+
+
+def rqa_set_bracket_model(ctx: Context, params, margin: float = 0.0):
+    import torch
+    _check(lib().rqa_set_bracket_model(ctx.handle,
+                                       _dev_ptr(params, torch.float32, RQA_MLP_PARAMS, "params"),
+                                       float(margin)), "rqa_set_bracket_model")
+
+
+def rqa_bracket_stats(ctx: Context):
+    h, m = c_u64(), c_u64()
+    _check(lib().rqa_bracket_stats(ctx.handle, ctypes.byref(h), ctypes.byref(m)), "rqa_bracket_stats")
+    return int(h.value), int(m.value)

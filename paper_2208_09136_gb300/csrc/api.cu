@@ -8,6 +8,8 @@
 #include <vector>
 
 #include "rqa.h"
+#include "rqa_learn.h"
+#include "rqa_learn_internal.h"
 #include "rqa_common.cuh"
 
 using namespace rqa;
@@ -53,9 +55,16 @@ struct rqa_ctx {
 
     // scratch (grow-only)
     DevBuf arena;      // uploaded plan: series, targets, items, lmin, hist offsets
-    DevBuf prefix, level, rank, below, tab_sub, tab_mid, tab_fin1, tab_fin2, ngroups, hist;
+    DevBuf prefix, level, rank, below, tab_sub, tab_mid, tab_fin1, tab_fin2, ngroups, hist, krange;
     DevBuf queue, status;
     DevBuf eps_tmp, le_tmp, lt_tmp, count, lmax, hshort;
+
+    // learned bracket
+    DevBuf mlp;                 // installed network parameters
+    bool has_model = false;
+    float margin = 0.f;
+    DevBuf feats, centre, ymlp, acts, bstats, learn_scratch;
+    uint64_t sketch_seed = 1;
 
     // per-phase timing of the last call (batched schedule)
     bool timing = false;
@@ -349,6 +358,7 @@ int ensure_select_bufs(rqa_ctx *c, int S, int K)
     if ((rc = ensure(c->tab_fin1, (size_t)S * NCOARSE))) return rc;
     if ((rc = ensure(c->tab_fin2, (size_t)S * KMAX * NFINE))) return rc;
     if ((rc = ensure(c->ngroups, (size_t)S * 4 * sizeof(int32_t)))) return rc;
+    if ((rc = ensure(c->krange, (size_t)S * 2 * sizeof(uint32_t)))) return rc;
     if ((rc = ensure(c->hist, (size_t)S * hist_stride(K) * 8))) return rc;
     if ((rc = ensure(c->eps_tmp, sk * 4))) return rc;
     if ((rc = ensure(c->le_tmp, sk * 8))) return rc;
@@ -374,6 +384,7 @@ SelBufs sel_bufs(rqa_ctx *c, const Plan &pl)
     sb.n_fin = ng + 2 * pl.S;
     sb.hist = P<uint64_t>(c->hist);
     sb.hstride = hist_stride(pl.K);
+    sb.range = P<uint32_t>(c->krange);
     return sb;
 }
 
@@ -387,9 +398,10 @@ int reset_queue(rqa_ctx *c, int n, unsigned **q)
     return RQA_OK;
 }
 
-// Radix selection for series [s0, s0+ns) using the given item list.
+// Exact selection for series [s0, s0+ns) using the given item list: three
+// counting rounds, the first one split by the learned bracket if asked.
 int run_select(rqa_ctx *c, const Plan &pl, const SelBufs &sb, const Item *items, int n_items,
-               int s0, int ns, unsigned *&q, float *eps, uint64_t *le, uint64_t *lt)
+               int s0, int ns, unsigned *&q, float *eps, uint64_t *le, uint64_t *lt, bool bracket)
 {
     const int K = pl.K;
     const int grid = persistent_grid(c, (size_t)n_items);
@@ -402,7 +414,23 @@ int run_select(rqa_ctx *c, const Plan &pl, const SelBufs &sb, const Item *items,
     a.status = P<int>(c->status);
     const size_t hbytes = (size_t)ns * sb.hstride * 8;
     uint64_t *hbase = sb.hist + (int64_t)s0 * sb.hstride;
-    const int rounds[3] = {R_COARSE, R_MID, R_FINAL};
+    if (bracket) {
+        float *feats = P<float>(c->feats) + (int64_t)s0 * FEATURES;
+        float *centre = P<float>(c->centre) + s0;
+        float *ym = P<float>(c->ymlp) + (int64_t)s0 * MLP_OUT;
+        if (int rc = launched(c, launch_sketch(pl.y, pl.d_sd, s0, ns, c->sketch_seed, feats, centre,
+                                               nullptr, c->stream)))
+            return rc;
+        if (int rc = check_cuda(mlp_forward(P<float>(c->mlp), feats, ns, ym, P<float>(c->acts),
+                                            c->stream)))
+            return rc;
+        c->launches += 3;
+        if (int rc = launched(c, launch_bracket(ym, centre, c->margin, ns, K,
+                                                sb.tab_sub + (int64_t)s0 * NCOARSE, sb.n_sub + s0,
+                                                c->stream)))
+            return rc;
+    }
+    const int rounds[3] = {bracket ? R_COARSE_SUB : R_COARSE, R_MID, R_FINAL};
     for (int r = 0; r < 3; ++r) {
         if (int rc = check_cuda(cudaMemsetAsync(hbase, 0, hbytes, c->stream))) return rc;
         a.queue = q;
@@ -411,14 +439,43 @@ int run_select(rqa_ctx *c, const Plan &pl, const SelBufs &sb, const Item *items,
         if (int rc = launched(c, launch_select(rounds[r], sb, pl.d_sd, s0, ns, K, eps, le, lt,
                                                P<int>(c->status), c->stream)))
             return rc;
+        if (bracket && r == 0)
+            if (int rc = launched(c, launch_bracket_stats(sb.level + (int64_t)s0 * K, (int64_t)ns * K,
+                                                          P<unsigned long long>(c->bstats), c->stream)))
+                return rc;
         mark(c, 2 + r);
     }
     return RQA_OK;
 }
 
-int select_all(rqa_ctx *c, const rqa_batch *b, Plan &pl, float *eps, uint64_t *le, uint64_t *lt)
+// Whether this call's targets are the ones the bracket network predicts.
+bool rr_matches_model(const int32_t *rr_num, int32_t rr_den, int K)
+{
+    if (K != MLP_K || !rr_num) return false;
+    for (int k = 0; k < K; ++k)
+        if ((int64_t)rr_num[k] * 100 != (int64_t)(k + 1) * rr_den) return false;
+    return true;
+}
+
+int ensure_bracket_bufs(rqa_ctx *c, int S)
+{
+    int rc = RQA_OK;
+    if ((rc = ensure(c->feats, (size_t)S * FEATURES * 4))) return rc;
+    if ((rc = ensure(c->centre, (size_t)S * 4))) return rc;
+    if ((rc = ensure(c->ymlp, (size_t)S * MLP_OUT * 4))) return rc;
+    if ((rc = ensure(c->acts, (size_t)S * 2 * HIDDEN * 4))) return rc;
+    if ((rc = ensure(c->bstats, 16))) return rc;
+    return RQA_OK;
+}
+
+int select_all(rqa_ctx *c, const rqa_batch *b, Plan &pl, float *eps, uint64_t *le, uint64_t *lt,
+               bool bracket)
 {
     const SelBufs sb = sel_bufs(c, pl);
+    if (bracket) {
+        if (int rc = ensure_bracket_bufs(c, pl.S)) return rc;
+        if (int rc = check_cuda(cudaMemsetAsync(c->bstats.p, 0, 16, c->stream))) return rc;
+    }
     mark(c, 0);
     if (int rc = launched(c, launch_check_finite(b->y, pl.total, P<int>(c->status), c->stream)))
         return rc;
@@ -431,13 +488,14 @@ int select_all(rqa_ctx *c, const rqa_batch *b, Plan &pl, float *eps, uint64_t *l
         if (int rc = reset_queue(c, 3 * pl.S, &q)) return rc;
         for (int s = 0; s < pl.S; ++s) {
             const int ib = pl.ser_begin[s], ie = pl.ser_begin[s + 1];
-            if (int rc = run_select(c, pl, sb, pl.d_ser + ib, ie - ib, s, 1, q, eps, le, lt))
+            if (int rc = run_select(c, pl, sb, pl.d_ser + ib, ie - ib, s, 1, q, eps, le, lt, bracket))
                 return rc;
         }
         return RQA_OK;
     }
     if (int rc = reset_queue(c, 3, &q)) return rc;
-    return run_select(c, pl, sb, pl.d_lpt, (int)pl.items_lpt.size(), 0, pl.S, q, eps, le, lt);
+    return run_select(c, pl, sb, pl.d_lpt, (int)pl.items_lpt.size(), 0, pl.S, q, eps, le, lt,
+                      bracket);
 }
 
 int ensure_line_bufs(rqa_ctx *c, int S, int K)
@@ -544,6 +602,18 @@ int validate_hist(const rqa_batch *b, int K, const uint64_t *hist, const int64_t
     return RQA_OK;
 }
 
+// Selection mode of a call: bracket with a model and matching targets.
+int use_bracket(rqa_ctx *c, const int32_t *rr_num, int32_t rr_den, int K, bool *out)
+{
+    *out = false;
+    if (c->select == RQA_SELECT_RADIX) return RQA_OK;
+    if (c->select == RQA_SELECT_BRACKET && !c->has_model) return RQA_ERR_NO_MODEL;
+    const bool match = rr_matches_model(rr_num, rr_den, K);
+    if (c->select == RQA_SELECT_BRACKET && !match) return RQA_ERR_INVALID_ARG;
+    *out = c->has_model && match;
+    return RQA_OK;
+}
+
 }  // namespace
 
 // ====================================================================== ABI
@@ -635,9 +705,11 @@ void rqa_destroy(rqa_ctx *c)
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->arena, &c->prefix, &c->level, &c->rank, &c->below, &c->tab_sub,
-                      &c->tab_mid, &c->tab_fin1, &c->tab_fin2, &c->ngroups, &c->hist, &c->queue,
+                      &c->tab_mid, &c->tab_fin1, &c->tab_fin2, &c->ngroups, &c->hist, &c->krange,
+                      &c->queue,
                       &c->status, &c->eps_tmp, &c->le_tmp, &c->lt_tmp, &c->count, &c->lmax,
-                      &c->hshort};
+                      &c->hshort, &c->mlp, &c->feats, &c->centre, &c->ymlp, &c->acts,
+                      &c->bstats, &c->learn_scratch};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -675,13 +747,14 @@ int rqa_eps_for_rr(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_
     if (!c || !eps_out) return RQA_ERR_INVALID_ARG;
     if (int rc = validate_batch(b)) return rc;
     if (int rc = validate_rr(rr_num, rr_den, K)) return rc;
-    if (c->select == RQA_SELECT_BRACKET) return RQA_ERR_NO_MODEL;
+    bool bracket = false;
+    if (int rc = use_bracket(c, rr_num, rr_den, K, &bracket)) return rc;
     cudaSetDevice(c->device);
     Plan pl;
     if (int rc = make_plan(c, b, rr_num, rr_den, K, pl)) return rc;
     if (int rc = ensure_select_bufs(c, pl.S, K)) return rc;
     if (int rc = upload_plan(c, pl, nullptr, 0, nullptr)) return rc;
-    return select_all(c, b, pl, eps_out, count_le, count_lt);
+    return select_all(c, b, pl, eps_out, count_le, count_lt, bracket);
 }
 
 int rqa_det_avg(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_den,
@@ -695,9 +768,10 @@ int rqa_det_avg(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t r
     if (int rc = validate_batch(b)) return rc;
     if (lo)
         if (int rc = validate_hist(b, K, lo->hist, lo->hist_offsets)) return rc;
+    bool bracket = false;
     if (!eps) {
         if (int rc = validate_rr(rr_num, rr_den, K)) return rc;
-        if (c->select == RQA_SELECT_BRACKET) return RQA_ERR_NO_MODEL;
+        if (int rc = use_bracket(c, rr_num, rr_den, K, &bracket)) return rc;
     }
     cudaSetDevice(c->device);
     Plan pl;
@@ -710,7 +784,7 @@ int rqa_det_avg(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t r
     const float *e = eps;
     if (!eps) {
         if (int rc = select_all(c, b, pl, P<float>(c->eps_tmp), P<uint64_t>(c->le_tmp),
-                                P<uint64_t>(c->lt_tmp)))
+                                P<uint64_t>(c->lt_tmp), bracket))
             return rc;
         e = P<float>(c->eps_tmp);
     } else {
@@ -783,5 +857,84 @@ int rqa_phase_times(rqa_ctx *c, float *ms, int n)
 }
 
 uint64_t rqa_kernel_launches(rqa_ctx *c) { return c ? c->launches : 0; }
+
+// ---------------------------------------------------------- learned bracket
+int rqa_sketch(rqa_ctx *c, const rqa_batch *b, uint64_t seed, float *feats, float *centre,
+               float *qdist)
+{
+    if (!c || !feats) return RQA_ERR_INVALID_ARG;
+    if (int rc = validate_batch(b)) return rc;
+    cudaSetDevice(c->device);
+    Plan pl;
+    if (int rc = make_plan(c, b, nullptr, 0, 1, pl)) return rc;
+    if (int rc = upload_plan(c, pl, nullptr, 0, nullptr)) return rc;
+    return launched(c, launch_sketch(b->y, pl.d_sd, 0, pl.S, seed, feats, centre, qdist, c->stream));
+}
+
+int rqa_mlp_forward(rqa_ctx *c, const float *params, const float *X, int32_t B, float *Y,
+                    float *acts)
+{
+    if (!c || !params || !X || !Y || B < 1) return RQA_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    if (!acts) {
+        if (int rc = ensure(c->learn_scratch, (size_t)B * 2 * HIDDEN * 4)) return rc;
+        acts = P<float>(c->learn_scratch);
+    }
+    c->launches += 3;
+    return check_cuda(mlp_forward(params, X, B, Y, acts, c->stream));
+}
+
+int rqa_mlp_backward(rqa_ctx *c, const float *params, const float *X, const float *acts,
+                     const float *Y, const float *T, int32_t B, float tau_lo, float tau_hi,
+                     float *grads, float *loss)
+{
+    if (!c || !params || !X || !acts || !Y || !T || !grads || B < 1) return RQA_ERR_INVALID_ARG;
+    if (!(tau_lo > 0.f && tau_lo < 1.f && tau_hi > 0.f && tau_hi < 1.f)) return RQA_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    if (int rc = ensure(c->learn_scratch, (size_t)B * (MLP_OUT + 2 * HIDDEN) * 4)) return rc;
+    c->launches += 10;
+    return check_cuda(mlp_backward(params, X, acts, Y, T, B, tau_lo, tau_hi, grads, loss,
+                                   P<float>(c->learn_scratch), c->stream));
+}
+
+int rqa_adam_step(rqa_ctx *c, float *params, const float *grads, float *m, float *v, int64_t n,
+                  int32_t t, float lr, float beta1, float beta2, float eps)
+{
+    if (!c || !params || !grads || !m || !v || n < 1 || t < 1) return RQA_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    return launched(c, adam_step(params, grads, m, v, n, t, lr, beta1, beta2, eps, c->stream));
+}
+
+int rqa_set_bracket_model(rqa_ctx *c, const float *params, float margin)
+{
+    if (!c || !(margin >= 0.f)) return RQA_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    if (!params) {
+        c->has_model = false;
+        return RQA_OK;
+    }
+    if (int rc = ensure(c->mlp, (size_t)MLP_PARAMS * 4)) return rc;
+    if (int rc = check_cuda(cudaMemcpyAsync(c->mlp.p, params, (size_t)MLP_PARAMS * 4,
+                                            cudaMemcpyDeviceToDevice, c->stream)))
+        return rc;
+    c->has_model = true;
+    c->margin = margin;
+    return RQA_OK;
+}
+
+int rqa_bracket_stats(rqa_ctx *c, uint64_t *hits, uint64_t *misses)
+{
+    if (!c) return RQA_ERR_INVALID_ARG;
+    uint64_t hm[2] = {0, 0};
+    if (c->bstats.p) {
+        cudaSetDevice(c->device);
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(cudaGetLastError());
+        if (cudaMemcpy(hm, c->bstats.p, 16, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return check_cuda(cudaGetLastError());
+    }
+    if (hits) *hits = hm[0];
+    if (misses) *misses = hm[1];
+    return RQA_OK;
+}
 
 }  // extern "C"

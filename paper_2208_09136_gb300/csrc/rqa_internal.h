@@ -55,6 +55,7 @@ struct SelBufs {
     int8_t *tab_fin1;      // [s][NCOARSE] coarse bucket -> final super group, -1
     int8_t *tab_fin2;      // [s][KMAX][NFINE] (super group, middle digit) -> group
     int32_t *n_sub, *n_mid, *n_fin;   // [s]
+    uint32_t *range;       // [s][2]: keys the next filtered round can count, inclusive
     uint64_t *hist;        // [s][hstride]: NCOARSE coarse bins then fine bins
     int64_t hstride;
 };

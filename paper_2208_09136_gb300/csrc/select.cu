@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
     __shared__ int slot;
     __shared__ int nb_used_sh;
     __shared__ int next_band;
+    __shared__ uint32_t key_lo, key_hi;
     const int nbins_max = (ROUND == R_COARSE) ? NCOARSE
                         : (ROUND == R_COARSE_SUB) ? NCOARSE + NSUB_MAX * NFINE
                                                   : K * NFINE;
@@ -100,6 +101,12 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
             else nb = sb.n_fin[item.s] * NFINE;
             nb_used_sh = nb;
             next_band = item.b_lo;
+            key_lo = 0u;
+            key_hi = 0xffffffffu;
+            if (ROUND == R_MID || ROUND == R_FINAL) {
+                key_lo = sb.range[2 * (int64_t)item.s];
+                key_hi = sb.range[2 * (int64_t)item.s + 1];
+            }
         }
         __syncthreads();
         const int nb_used = nb_used_sh;
@@ -117,6 +124,7 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
         }
 
         const float *ys = a.y + sd.off;
+        const uint32_t klo = key_lo, khi = key_hi;
         for (;;) {
             // bands are handed to warps one at a time, so no warp idles while
             // another still has several bands of the item left
@@ -139,6 +147,9 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
                     if (i < sd.ne - dl) {
                         const uint32_t key =
                             __float_as_uint(tile.dist(ys, j, i, dl, sd.tau, sd.m));
+                        // filtered rounds: most keys fall outside every group
+                        if ((ROUND == R_MID || ROUND == R_FINAL) && (key < klo || key > khi))
+                            continue;
                         const int bin = bin_of<ROUND>(key, t1, t2);
                         if (bin >= 0) {
                             // consecutive cells of a lane are neighbours in the
@@ -350,11 +361,16 @@ k_select(SelBufs sb, const SeriesDev *series, int s_begin, int K, float *eps_out
         __syncthreads();
         if (t == 0) {
             int g = 0;
+            uint32_t lo = 0xffffffffu, hi = 0u;
             for (int k = 0; k < K; ++k) {
                 if (lev[k] != 1) continue;
                 if (tm[pre[k]] < 0) tm[pre[k]] = (int8_t)g++;
+                lo = min(lo, pre[k] << COARSE_SHIFT);
+                hi = max(hi, ((pre[k] + 1u) << COARSE_SHIFT) - 1u);
             }
             sb.n_mid[s] = g;
+            sb.range[2 * (int64_t)s] = lo;
+            sb.range[2 * (int64_t)s + 1] = hi;
         }
         if (t < K) {
             sb.prefix[sk + t] = pre[t];
@@ -403,13 +419,18 @@ k_select(SelBufs sb, const SeriesDev *series, int s_begin, int K, float *eps_out
         __syncthreads();
         if (t == 0) {
             int g1 = 0, g = 0;
+            uint32_t lo = 0xffffffffu, hi = 0u;
             for (int k = 0; k < K; ++k) {
                 const uint32_t c = pre[k] >> 10, mid = pre[k] & (NFINE - 1);
                 if (f1[c] < 0) f1[c] = (int8_t)g1++;
                 int8_t *e = f2 + f1[c] * NFINE + mid;
                 if (*e < 0) *e = (int8_t)g++;
+                lo = min(lo, pre[k] << 10);
+                hi = max(hi, ((pre[k] + 1u) << 10) - 1u);
             }
             sb.n_fin[s] = g;
+            sb.range[2 * (int64_t)s] = lo;
+            sb.range[2 * (int64_t)s + 1] = hi;
         }
         if (t < K) {
             sb.prefix[sk + t] = pre[t];

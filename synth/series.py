@@ -158,21 +158,24 @@ def make_series(spec: SeriesSpec, cache: bool = True) -> np.ndarray:
 
 
 def _make_many(specs: Sequence[SeriesSpec], cache: bool = True) -> List[np.ndarray]:
-    """Like make_series over a list, integrating uncached Lorenz runs of equal
-    length as one RK4 batch (identical arithmetic per series)."""
+    """Like make_series over a list.  All uncached Lorenz runs are integrated
+    as one RK4 batch up to the longest of them; each series keeps its own
+    first N samples, so the arithmetic per series is that of a lone run."""
     out: List[np.ndarray] = [None] * len(specs)  # type: ignore
-    pending: Dict[int, List[int]] = {}
+    pending: List[int] = []
     for idx, sp in enumerate(specs):
-        if sp.kind == "lorenz" and sp.n >= 5000 and not (cache and os.path.exists(_cache_path(sp))):
-            pending.setdefault(sp.n, []).append(idx)
+        if sp.kind == "lorenz" and not (cache and os.path.exists(_cache_path(sp))):
+            pending.append(idx)
         else:
             out[idx] = make_series(sp, cache=cache)
-    for n, idxs in pending.items():
-        rngs = [specs[i].rng() for i in idxs]
+    if pending:
+        rngs = [specs[i].rng() for i in pending]
         x0 = np.stack([np.array([1.0, 1.0, 1.0]) + 0.1 * r.standard_normal(3) for r in rngs])
-        xs = _lorenz_batch(x0, n)
-        for row, (i, r) in enumerate(zip(idxs, rngs)):
-            x = xs[row]
+        n_max = max(specs[i].n for i in pending)
+        xs = _lorenz_batch(x0, n_max)
+        for row, (i, r) in enumerate(zip(pending, rngs)):
+            n = specs[i].n
+            x = xs[row, :n]
             clean = (x - x.mean()) / x.std()
             y = add_noise_db(clean, specs[i].snr_db, r).astype(np.float32)
             out[i] = y

@@ -1,0 +1,164 @@
+"""GPU checks of the learned bracket: sketch, network forward/backward and
+Adam against the FP64 oracle, and exactness of bracketed selection (with an
+untrained and, when present, the trained network)."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as MO
+from tests._helpers import RR20, oracle_series
+
+pytestmark = pytest.mark.gpu
+
+
+def _series(seed, sizes, kind="mix"):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i, n in enumerate(sizes):
+        t = np.arange(n)
+        if i % 2:
+            out.append(rng.standard_normal(n).astype(np.float32))
+        else:
+            out.append((np.sin(2 * np.pi * t / 20.3) + 0.2 * rng.standard_normal(n)).astype(np.float32))
+    return out
+
+
+def test_sketch_matches_oracle(rqa_lib):
+    import torch
+    rqa = rqa_lib
+    ys = _series(1, [50, 300, 1000, 4097, 20000])
+    ctx = rqa.Context()
+    batch = rqa.Batch.from_numpy(ys, [3, 1, 3, 2, 3], [3, 1, 1, 5, 3])
+    S = batch.n_series
+    feats = torch.empty((S, 131), dtype=torch.float32, device="cuda")
+    centre = torch.empty(S, dtype=torch.float32, device="cuda")
+    qd = torch.empty((S, 128), dtype=torch.float32, device="cuda")
+    rqa.rqa_sketch(ctx, batch, 12345, feats, centre, qd)
+    assert rqa.rqa_status(ctx) == 0
+    f, c, q = feats.cpu().numpy(), centre.cpu().numpy(), qd.cpu().numpy()
+    for s in range(S):
+        x, cc, qq = MO.sketch_features(ys[s], int(batch.m[s]), int(batch.tau[s]), s, 12345)
+        assert np.array_equal(q[s], qq)                 # sampled distances: exact
+        assert abs(c[s] - cc) <= 2e-6 * max(1.0, abs(cc))
+        assert np.allclose(f[s], x, rtol=1e-5, atol=2e-6)
+
+
+def _oracle_params(seed=3):
+    return MO.init_params(seed)
+
+
+def test_mlp_forward_backward_adam(rqa_lib):
+    import torch
+    rqa = rqa_lib
+    ctx = rqa.Context()
+    rng = np.random.default_rng(9)
+    compared = 0
+    for B in (1, 37, 256, 300):
+        p = (_oracle_params() * 0.5).astype(np.float32)
+        X = rng.standard_normal((B, 131)).astype(np.float32)
+        T = rng.standard_normal((B, 20)).astype(np.float32)
+        dp = torch.from_numpy(p).cuda()
+        dX = torch.from_numpy(X).cuda()
+        dT = torch.from_numpy(T).cuda()
+        Y = torch.empty((B, 40), dtype=torch.float32, device="cuda")
+        acts = torch.empty((B, 512), dtype=torch.float32, device="cuda")
+        rqa.rqa_mlp_forward(ctx, dp, dX, Y, acts)
+        ref = MO.forward(p, X)
+        y = Y.cpu().numpy()
+        scale = np.abs(ref["Y"]).max()
+        assert np.abs(y - ref["Y"]).max() <= 1e-5 * scale + 1e-6
+        a = acts.cpu().numpy()
+        assert np.allclose(a[:, :256].ravel(), ref["H1"].ravel(), rtol=1e-4, atol=1e-5 * np.abs(ref["H1"]).max())
+        g = torch.empty_like(dp)
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        rqa.rqa_mlp_backward(ctx, dp, dX, acts, Y, dT, 0.05, 0.95, g, loss)
+        rl, rg = MO.backward(p, X, T, 0.05, 0.95)
+        gg = g.cpu().numpy()
+        assert abs(float(loss.item()) - rl) <= 1e-4 * max(1.0, abs(rl))
+        # A unit whose pre-activation rounds to the other side of zero in FP32
+        # (or an output exactly on a loss kink) changes the gradient by design;
+        # compare only batches where both sides took the same branches.
+        same = (np.array_equal(a[:, :256] > 0, ref["H1"] > 0) and
+                np.array_equal(a[:, 256:] > 0, ref["H2"] > 0) and
+                np.array_equal(np.repeat(T, 2, axis=1) >= y, np.repeat(T, 2, axis=1) >= ref["Y"]))
+        if same:
+            compared += 1
+            assert np.abs(gg - rg).max() <= 2e-4 * np.abs(rg).max() + 1e-7
+        # one Adam step
+        m = torch.zeros_like(dp)
+        v = torch.zeros_like(dp)
+        p2 = dp.clone()
+        rqa.rqa_adam_step(ctx, p2, g, m, v, 1, 1e-3)
+        ref_p, _, _ = MO.adam(p.astype(np.float64), gg.astype(np.float64), 0.0, 0.0, 1, lr=1e-3)
+        assert np.allclose(p2.cpu().numpy(), ref_p, rtol=1e-5, atol=1e-6)
+    assert compared >= 3
+    assert rqa.rqa_status(ctx) == 0
+
+
+def _select(rqa, ys, m, tau, model, schedule=0):
+    import torch
+    ctx = rqa.Context(schedule=schedule, select=rqa.RQA_SELECT_BRACKET if model is not None
+                      else rqa.RQA_SELECT_RADIX)
+    if model is not None:
+        rqa.rqa_set_bracket_model(ctx, torch.from_numpy(model).cuda(), 0.05)
+    batch = rqa.Batch.from_numpy(ys, m, tau)
+    out = rqa.eps_for_rr(ctx, batch, RR20, 100)
+    da = rqa.det_avg(ctx, batch, RR20, 100, lmin=(2, 3, 5))
+    code = rqa.rqa_status(ctx)
+    assert code == 0, rqa.rqa_error_string(code)
+    stats = rqa.rqa_bracket_stats(ctx) if model is not None else None
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    res.update(det=da["det"].cpu().numpy(), det_avg=da["det_avg"].cpu().numpy())
+    ctx.close()
+    return res, stats
+
+
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_bracketed_selection_exact_with_untrained_model(rqa_lib, schedule):
+    """A random network misses most intervals: every threshold must still be
+    exact (the full selection takes over)."""
+    ys = _series(4, [120, 900, 3000, 7000, 64])
+    model = MO.init_params(11)
+    got, (hits, misses) = _select(rqa_lib, ys, 3, 3, model, schedule)
+    base, _ = _select(rqa_lib, ys, 3, 3, None, schedule)
+    for key in ("eps", "count_le", "count_lt", "det", "det_avg"):
+        assert np.array_equal(got[key], base[key]), key
+    assert hits + misses == len(ys) * 20
+    for s, y in enumerate(ys):
+        ref = oracle_series(y, 3, 3, RR20, 100, lmin=(2, 3, 5), full_hist=False)
+        assert np.array_equal(got["eps"][s], ref["eps"])
+        assert np.array_equal(got["det"][s], ref["det"])
+
+
+def test_bracket_rejects_other_targets(rqa_lib):
+    import torch
+    rqa = rqa_lib
+    ctx = rqa.Context(select=rqa.RQA_SELECT_BRACKET)
+    batch = rqa.Batch.from_numpy(_series(2, [200]), 3, 3)
+    with pytest.raises(rqa.RqaError) as ei:
+        rqa.eps_for_rr(ctx, batch, RR20, 100)
+    assert ei.value.code == 9  # no model installed
+    rqa.rqa_set_bracket_model(ctx, torch.from_numpy(MO.init_params(1)).cuda(), 0.0)
+    with pytest.raises(rqa.RqaError):
+        rqa.eps_for_rr(ctx, batch, list(range(1, 11)), 100)  # the network predicts 20 targets
+    ctx.close()
+
+
+def test_trained_model_hits_and_stays_exact(rqa_lib):
+    """The trained network on held-out long Lorenz series (N = 10^5,
+    m = tau = 3, SNR -10/0/10 dB): thresholds equal the radix selection bit
+    for bit, and most intervals hold (each miss costs one extra pass)."""
+    from paper_2208_09136_gb300 import bracket
+    if not os.path.exists(bracket.MODEL_PATH):
+        pytest.skip("no trained model file")
+    from synth import workload
+    w = workload("lorenz-n1e5-eval")
+    ys = w.series()
+    model = bracket.load_model()["params"]
+    got, (hits, misses) = _select(rqa_lib, ys, 3, 3, model)
+    base, _ = _select(rqa_lib, ys, 3, 3, None)
+    for key in ("eps", "count_le", "count_lt", "det", "det_avg"):
+        assert np.array_equal(got[key], base[key]), key
+    assert hits + misses == 60
+    assert hits >= 54, (hits, misses)
