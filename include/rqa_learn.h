@@ -47,8 +47,9 @@ extern "C" {
 int rqa_sketch(rqa_ctx *ctx, const rqa_batch *batch, uint64_t seed, float *feats,
                float *centre, float *qdist);
 
-/* Network forward pass for B rows.  X: B x 131, Y: B x 40.  acts: B x 512
- * hidden activations for rqa_mlp_backward (may be NULL). */
+/* Network forward pass for B rows.  X: B x 131, Y: B x 40.  acts: 512 B
+ * floats receiving the hidden activations for rqa_mlp_backward: layer 1
+ * (B x 256, row-major) followed by layer 2 (B x 256); may be NULL. */
 int rqa_mlp_forward(rqa_ctx *ctx, const float *params, const float *X, int32_t B, float *Y,
                     float *acts);
 
