@@ -205,6 +205,38 @@ int rqa_line_hist(rqa_ctx *ctx, const rqa_batch *batch, const float *eps, int32_
                   uint64_t *hist, const int64_t *hist_offsets, uint32_t *lmax,
                   uint64_t *count, uint64_t *stencil);
 
+/* ---- selection without allocation ---------------------------------------
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory at the time they need thresholds, for
+ * example an application whose own allocator owns the whole device, or a
+ * latency-bound host thread that cannot afford the device-wide
+ * synchronisation of cudaMalloc/cudaFree.  It computes the same thresholds
+ * and counts as rqa_eps_for_rr (bit for bit), for at most
+ * RQA_NOALLOC_MAX_SERIES series, without a context and without allocating:
+ * its histograms, tables, work items and counters live in one fixed device
+ * array of RQA_NOALLOC_SCRATCH_BYTES inside the library, which every device
+ * that loads the library keeps until the process exits.
+ *   - Runs on the current CUDA device and the given stream (NULL = default).
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) and the SM count; make that first call before
+ *     any stream capture.
+ *   - All calls on a device share the array and each call overwrites it;
+ *     calls whose work overlaps on the GPU (other streams, other host
+ *     threads) race and give wrong results.  Order them on one stream.
+ *   - batch->y, eps_out, count_le, count_lt: device, as in rqa_eps_for_rr;
+ *     count_le / count_lt may be NULL.
+ *   - status_out: device int (may be NULL) that receives the device-side
+ *     status of the call (RQA_OK, RQA_ERR_NONFINITE, ...) when it completes.
+ *   - Returns RQA_ERR_CAPACITY for more than RQA_NOALLOC_MAX_SERIES series,
+ *     and the argument errors of rqa_eps_for_rr; nothing is enqueued then.
+ */
+#define RQA_NOALLOC_MAX_SERIES 4
+#define RQA_NOALLOC_SCRATCH_BYTES 1310720 /* 1.25 MiB */
+int rqa_eps_for_rr_noalloc(const rqa_batch *batch, const int32_t *rr_num, int32_t rr_den,
+                           int32_t K, float *eps_out, uint64_t *count_le, uint64_t *count_lt,
+                           int *status_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,8 @@ _SIGS = {
                        ctypes.c_float, ctypes.c_float], c_int),
     "rqa_set_bracket_model": ([c_vp, c_vp, ctypes.c_float], c_int),
     "rqa_bracket_stats": ([c_vp, c_vp, c_vp], c_int),
+    "rqa_eps_for_rr_noalloc": ([ctypes.POINTER(_Batch), c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp,
+                                c_vp], c_int),
 }
 
 
@@ -361,3 +363,26 @@ def rqa_bracket_stats(ctx: Context):
     h, m = c_u64(), c_u64()
     _check(lib().rqa_bracket_stats(ctx.handle, ctypes.byref(h), ctypes.byref(m)), "rqa_bracket_stats")
     return int(h.value), int(m.value)
+
+
+# ------------------------------------------------------------ no allocation
+RQA_NOALLOC_MAX_SERIES = 4
+
+
+def rqa_eps_for_rr_noalloc(batch: Batch, rr_num, rr_den: int, eps_out, count_le=None,
+                           count_lt=None, status_out=None, stream=None):
+    """Thresholds without any device allocation (see rqa.h): at most
+    RQA_NOALLOC_MAX_SERIES series, on the current device and the given torch
+    stream (default: the current stream)."""
+    import torch
+    rr = np.ascontiguousarray(rr_num, dtype=np.int32)
+    n = batch.n_series * len(rr)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    b = batch._c()
+    _check(lib().rqa_eps_for_rr_noalloc(ctypes.byref(b), _np_ptr(rr), int(rr_den), len(rr),
+                                        _dev_ptr(eps_out, torch.float32, n, "eps_out"),
+                                        _dev_ptr(count_le, torch.uint64, n, "count_le"),
+                                        _dev_ptr(count_lt, torch.uint64, n, "count_lt"),
+                                        _dev_ptr(status_out, torch.int32, 1, "status_out"),
+                                        c_vp(stream.cuda_stream)), "rqa_eps_for_rr_noalloc")
