@@ -87,7 +87,8 @@ typedef struct {
     int band;          /* diagonals per warp band of the line pass: 0 = default
                           (8), else 4, 8 or 16 (4 and 16 only for (m, tau) =
                           (1, any), (3, 1), (3, 3); otherwise 8 is used) */
-    int blocks_per_sm; /* persistent CTAs per SM: 0 = tuned default */
+    int blocks_per_sm; /* persistent CTAs per SM: 0 = as many as each kernel
+                          can keep resident, else at most this many */
     int reserved[4];   /* must be zero */
 } rqa_config;
 
@@ -120,7 +121,8 @@ const char *rqa_error_string(int code);
 int rqa_abi_version(void);
 
 /* Number of SMs of the context's device and the schedule parameters in use
- * (band, blocks per SM); any pointer may be NULL. */
+ * (line-pass band width, blocks per SM as configured: 0 = resident limit);
+ * any pointer may be NULL. */
 int rqa_device_info(rqa_ctx *ctx, int *sm_count, int *band, int *blocks_per_sm);
 
 /* Per-phase device times of the context's last hot-path call, in ms, when

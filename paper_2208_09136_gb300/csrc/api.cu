@@ -186,9 +186,12 @@ int validate_rr(const int32_t *rr_num, int32_t rr_den, int32_t K)
     return RQA_OK;
 }
 
+// Requested persistent grid: every item its CTA, at most blocks_per_sm per SM
+// when the caller set it; the launchers further cap it at the CTAs the
+// kernel can keep resident.
 int persistent_grid(rqa_ctx *c, size_t n_items)
 {
-    const int bpsm = c->bpsm > 0 ? c->bpsm : 2;
+    const int bpsm = c->bpsm > 0 ? c->bpsm : 8;
     const size_t g = (size_t)c->sm_count * bpsm;
     return (int)std::max<size_t>(1, std::min(g, n_items));
 }
@@ -256,7 +259,7 @@ int make_plan(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_
     // warp work units (line pass): runs of `chunk` bands, series largest
     // first; about eight units per warp so the tail stays short while each
     // unit's histogram flush is spread over many cells
-    const int64_t n_warps = (int64_t)persistent_grid(c, (size_t)1 << 30) * WARPS;
+    const int64_t n_warps = (int64_t)c->sm_count * 2 * WARPS;  // resident warps of the line pass
     auto chunk_for = [&](int64_t bands) {
         return (int32_t)std::max<int64_t>(4, std::min<int64_t>(64, bands / (n_warps * 8)));
     };
@@ -737,7 +740,7 @@ int rqa_device_info(rqa_ctx *c, int *sm_count, int *band, int *blocks_per_sm)
     if (!c) return RQA_ERR_INVALID_ARG;
     if (sm_count) *sm_count = c->sm_count;
     if (band) *band = c->band_lines ? c->band_lines : DL_DEFAULT;
-    if (blocks_per_sm) *blocks_per_sm = c->bpsm > 0 ? c->bpsm : 2;
+    if (blocks_per_sm) *blocks_per_sm = c->bpsm;  // 0: as many as each kernel keeps resident
     return RQA_OK;
 }
 

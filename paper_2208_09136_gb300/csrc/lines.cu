@@ -327,6 +327,7 @@ static cudaError_t launch_lines_h(const CellArgs &a, const LineBufs &lb, int K, 
     const int smem = lines_smem_bytes(K);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
+    grid = persistent_cap(reinterpret_cast<const void *>(kern), smem, grid);
     kern<<<grid, THREADS, smem, st>>>(a, lb, K);
     return cudaGetLastError();
 }

@@ -39,6 +39,14 @@ struct BandTile {
             w[x] = (i < rows && idx < n) ? __ldg(ys + idx) : 0.f;
         }
     }
+    // every lane's row and window inside the series (an interior row block)
+    __device__ __forceinline__ void load_fast(const float *__restrict__ ys, int i, int d_lo, int)
+    {
+#pragma unroll
+        for (int q = 0; q < M; ++q) a[q] = __ldg(ys + i + q * TAU);
+#pragma unroll
+        for (int x = 0; x < D + (M - 1) * TAU; ++x) w[x] = __ldg(ys + i + d_lo + x);
+    }
     // cell (i, i + d_lo + j); only called for cells inside the triangle
     __device__ __forceinline__ float dist(const float *__restrict__, int j, int, int, int,
                                           int) const
@@ -62,6 +70,11 @@ struct BandTile<M, 0, D> {
             for (int q = 0; q < M; ++q) a[q] = __ldg(ys + i + q * tau);
         }
     }
+    __device__ __forceinline__ void load_fast(const float *__restrict__ ys, int i, int, int tau)
+    {
+#pragma unroll
+        for (int q = 0; q < M; ++q) a[q] = __ldg(ys + i + q * tau);
+    }
     __device__ __forceinline__ float dist(const float *__restrict__ ys, int, int i, int dl,
                                           int tau, int) const
     {
@@ -77,6 +90,7 @@ struct BandTile<M, 0, D> {
 template <int D>
 struct BandTile<0, 0, D> {
     __device__ __forceinline__ void load(const float *, int, int, int, int, int, int) {}
+    __device__ __forceinline__ void load_fast(const float *, int, int, int) {}
     __device__ __forceinline__ float dist(const float *__restrict__ ys, int, int i, int dl,
                                           int tau, int m) const
     {
@@ -91,6 +105,44 @@ struct BandTile<0, 0, D> {
 // Embedding variants with their own kernel instantiation.
 enum Embed : int { E_GENERIC = 0, E_M1 = 1, E_M2 = 2, E_M3 = 3, E_M4 = 4,
                    E_M1T1 = 11, E_M3T1 = 31, E_M3T3 = 33 };
+
+// Host: CTAs of `kern` (THREADS threads, `smem` dynamic bytes) resident per
+// SM, and the SM count of the current device; both cached per host thread.
+inline int resident_per_sm(const void *kern, int smem)
+{
+    struct Entry { const void *k; int s, v; };
+    static thread_local Entry cache[64];
+    static thread_local int n = 0;
+    for (int i = 0; i < n; ++i)
+        if (cache[i].k == kern && cache[i].s == smem) return cache[i].v;
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, THREADS, smem) != cudaSuccess) {
+        cudaGetLastError();
+        v = 1;
+    }
+    v = v < 1 ? 1 : v;
+    if (n < 64) cache[n++] = Entry{kern, smem, v};
+    return v;
+}
+
+inline int sm_count_current()
+{
+    static thread_local int cache[64] = {};
+    int d = 0;
+    cudaGetDevice(&d);
+    if (d >= 0 && d < 64 && cache[d]) return cache[d];
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d);
+    if (d >= 0 && d < 64) cache[d] = v;
+    return v;
+}
+
+// A persistent grid: at most the CTAs that can be resident at once.
+inline int persistent_cap(const void *kern, int smem, int grid)
+{
+    const int cap = sm_count_current() * resident_per_sm(kern, smem);
+    return grid < cap ? grid : (cap > 0 ? cap : 1);
+}
 
 // Fetch the next work item for this CTA (one atomic per CTA), -1 when done.
 __device__ __forceinline__ int next_item(unsigned int *queue, int n_items, int *sh_slot)

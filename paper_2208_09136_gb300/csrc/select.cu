@@ -137,32 +137,40 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
             const int rows = sd.ne - d_lo;
             int last = -1;
             uint32_t run = 0;
-            for (int i0 = 0; i0 < rows; i0 += 32) {
+            // one cell's key into the histogram; consecutive cells of a lane
+            // are neighbours in the matrix, so equal bins are aggregated
+            auto count_key = [&](uint32_t key) {
+                // filtered rounds: most keys fall outside every group
+                if ((ROUND == R_MID || ROUND == R_FINAL) && (key < klo || key > khi)) return;
+                const int bin = bin_of<ROUND>(key, t1, t2);
+                if (bin < 0) return;
+                if (bin == last) {
+                    ++run;
+                } else {
+                    if (run) atomicAdd(&h[last], run);
+                    last = bin;
+                    run = 1;
+                }
+            };
+            int i0 = 0;
+            // interior row blocks: every lane's cells on all BAND diagonals exist
+            for (; i0 + 32 <= rows - (BAND - 1); i0 += 32) {
+                const int i = i0 + lane;
+                BandTile<M, TAU, BAND> tile;
+                tile.load_fast(ys, i, d_lo, sd.tau);
+#pragma unroll
+                for (int j = 0; j < BAND; ++j)
+                    count_key(__float_as_uint(tile.dist(ys, j, i, d_lo + j, sd.tau, sd.m)));
+            }
+            for (; i0 < rows; i0 += 32) {
                 const int i = i0 + lane;
                 BandTile<M, TAU, BAND> tile;
                 tile.load(ys, sd.n, i, d_lo, rows, sd.tau, sd.m);
 #pragma unroll
                 for (int j = 0; j < BAND; ++j) {
                     const int dl = d_lo + j;
-                    if (i < sd.ne - dl) {
-                        const uint32_t key =
-                            __float_as_uint(tile.dist(ys, j, i, dl, sd.tau, sd.m));
-                        // filtered rounds: most keys fall outside every group
-                        if ((ROUND == R_MID || ROUND == R_FINAL) && (key < klo || key > khi))
-                            continue;
-                        const int bin = bin_of<ROUND>(key, t1, t2);
-                        if (bin >= 0) {
-                            // consecutive cells of a lane are neighbours in the
-                            // matrix: aggregate equal bins before the atomic
-                            if (bin == last) {
-                                ++run;
-                            } else {
-                                if (run) atomicAdd(&h[last], run);
-                                last = bin;
-                                run = 1;
-                            }
-                        }
-                    }
+                    if (i < sd.ne - dl)
+                        count_key(__float_as_uint(tile.dist(ys, j, i, dl, sd.tau, sd.m)));
                 }
             }
             if (run) atomicAdd(&h[last], run);
@@ -197,6 +205,7 @@ static cudaError_t launch_count_m(const CellArgs &a, const SelBufs &sb, int K, i
     }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
+    grid = persistent_cap(reinterpret_cast<const void *>(kern), smem, grid);
     kern<<<grid, THREADS, smem, st>>>(a, sb, K);
     return cudaGetLastError();
 }
