@@ -55,7 +55,8 @@ struct rqa_ctx {
 
     // scratch (grow-only)
     DevBuf arena;      // uploaded plan: series, targets, items, lmin, hist offsets
-    DevBuf prefix, level, rank, below, tab_sub, tab_mid, tab_fin1, tab_fin2, ngroups, hist, krange;
+    DevBuf prefix, level, rank, below, tab_sub, tab_mid, tab_fin1, tab_fin2, ngroups, hist, krange,
+        redo;
     DevBuf queue, status;
     DevBuf eps_tmp, le_tmp, lt_tmp, count, lmax, hshort;
 
@@ -362,6 +363,7 @@ int ensure_select_bufs(rqa_ctx *c, int S, int K)
     if ((rc = ensure(c->tab_fin2, (size_t)S * KMAX * NFINE))) return rc;
     if ((rc = ensure(c->ngroups, (size_t)S * 4 * sizeof(int32_t)))) return rc;
     if ((rc = ensure(c->krange, (size_t)S * 2 * sizeof(uint32_t)))) return rc;
+    if ((rc = ensure(c->redo, (size_t)S))) return rc;
     if ((rc = ensure(c->hist, (size_t)S * hist_stride(K) * 8))) return rc;
     if ((rc = ensure(c->eps_tmp, sk * 4))) return rc;
     if ((rc = ensure(c->le_tmp, sk * 8))) return rc;
@@ -388,6 +390,7 @@ SelBufs sel_bufs(rqa_ctx *c, const Plan &pl)
     sb.hist = P<uint64_t>(c->hist);
     sb.hstride = hist_stride(pl.K);
     sb.range = P<uint32_t>(c->krange);
+    sb.redo = P<uint8_t>(c->redo);
     return sb;
 }
 
@@ -430,11 +433,16 @@ int run_select(rqa_ctx *c, const Plan &pl, const SelBufs &sb, const Item *items,
         c->launches += 3;
         if (int rc = launched(c, launch_bracket(ym, centre, c->margin, ns, K,
                                                 sb.tab_sub + (int64_t)s0 * NCOARSE, sb.n_sub + s0,
-                                                c->stream)))
+                                                sb.range + 2 * (int64_t)s0, c->stream)))
             return rc;
+    } else {
+        // plain selection: the coarse round runs for every series
+        if (int rc = check_cuda(cudaMemsetAsync(sb.redo + s0, 1, (size_t)ns, c->stream))) return rc;
     }
-    const int rounds[3] = {bracket ? R_COARSE_SUB : R_COARSE, R_MID, R_FINAL};
-    for (int r = 0; r < 3; ++r) {
+    // bracket: split round, then the plain coarse round only for series with a
+    // target outside its bracket; then the middle and final rounds
+    const int rounds[4] = {R_COARSE_SUB, R_COARSE, R_MID, R_FINAL};
+    for (int r = bracket ? 0 : 1; r < 4; ++r) {
         if (int rc = check_cuda(cudaMemsetAsync(hbase, 0, hbytes, c->stream))) return rc;
         a.queue = q;
         q += 16;
@@ -442,11 +450,11 @@ int run_select(rqa_ctx *c, const Plan &pl, const SelBufs &sb, const Item *items,
         if (int rc = launched(c, launch_select(rounds[r], sb, pl.d_sd, s0, ns, K, eps, le, lt,
                                                P<int>(c->status), c->stream)))
             return rc;
-        if (bracket && r == 0)
+        if (r == 0)
             if (int rc = launched(c, launch_bracket_stats(sb.level + (int64_t)s0 * K, (int64_t)ns * K,
                                                           P<unsigned long long>(c->bstats), c->stream)))
                 return rc;
-        mark(c, 2 + r);
+        if (r >= 1) mark(c, 1 + r);
     }
     return RQA_OK;
 }
@@ -488,7 +496,7 @@ int select_all(rqa_ctx *c, const rqa_batch *b, Plan &pl, float *eps, uint64_t *l
         return rc;
     unsigned *q = nullptr;
     if (c->schedule == RQA_SCHED_PER_SERIES) {
-        if (int rc = reset_queue(c, 3 * pl.S, &q)) return rc;
+        if (int rc = reset_queue(c, 4 * pl.S, &q)) return rc;
         for (int s = 0; s < pl.S; ++s) {
             const int ib = pl.ser_begin[s], ie = pl.ser_begin[s + 1];
             if (int rc = run_select(c, pl, sb, pl.d_ser + ib, ie - ib, s, 1, q, eps, le, lt, bracket))
@@ -496,7 +504,7 @@ int select_all(rqa_ctx *c, const rqa_batch *b, Plan &pl, float *eps, uint64_t *l
         }
         return RQA_OK;
     }
-    if (int rc = reset_queue(c, 3, &q)) return rc;
+    if (int rc = reset_queue(c, 4, &q)) return rc;
     return run_select(c, pl, sb, pl.d_lpt, (int)pl.items_lpt.size(), 0, pl.S, q, eps, le, lt,
                       bracket);
 }
@@ -709,6 +717,7 @@ void rqa_destroy(rqa_ctx *c)
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->arena, &c->prefix, &c->level, &c->rank, &c->below, &c->tab_sub,
                       &c->tab_mid, &c->tab_fin1, &c->tab_fin2, &c->ngroups, &c->hist, &c->krange,
+                      &c->redo,
                       &c->queue,
                       &c->status, &c->eps_tmp, &c->le_tmp, &c->lt_tmp, &c->count, &c->lmax,
                       &c->hshort, &c->mlp, &c->feats, &c->centre, &c->ymlp, &c->acts,

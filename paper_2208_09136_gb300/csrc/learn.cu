@@ -279,7 +279,7 @@ cudaError_t adam_step(float *p, const float *g, float *m, float *v, int64_t n, i
 // buckets between the keys of exp(c + lo - margin) and exp(c + hi + margin);
 // if the union is larger than NSUB_MAX only each target's middle bucket.
 __global__ void k_bracket(const float *__restrict__ Yb, const float *__restrict__ centre,
-                          float margin, int K, int8_t *tab_sub, int32_t *n_sub)
+                          float margin, int K, int8_t *tab_sub, int32_t *n_sub, uint32_t *range)
 {
     __shared__ uint16_t lo_b[KMAX], hi_b[KMAX], mid_b[KMAX];
     __shared__ int8_t tb[NCOARSE];
@@ -319,9 +319,21 @@ __global__ void k_bracket(const float *__restrict__ Yb, const float *__restrict_
             for (int k = 0; k < K; ++k) tb[mid_b[k]] = 0;
         }
         int g = 0;  // marked buckets numbered in ascending order
-        for (int b = 0; b < NCOARSE; ++b)
-            if (tb[b] == 0) tb[b] = (g < NSUB_MAX) ? (int8_t)(g++) : (int8_t)-1;
+        int first = -1, last = -1;
+        for (int b = 0; b < NCOARSE; ++b) {
+            if (tb[b] != 0) continue;
+            if (g < NSUB_MAX) {
+                tb[b] = (int8_t)(g++);
+                if (first < 0) first = b;
+                last = b;
+            } else {
+                tb[b] = -1;
+            }
+        }
         n_sub[s] = g;
+        // keys the bracket round counts: from its first to its last split bucket
+        range[2 * s] = first < 0 ? 0xffffffffu : (uint32_t)first << COARSE_SHIFT;
+        range[2 * s + 1] = first < 0 ? 0u : (((uint32_t)last + 1u) << COARSE_SHIFT) - 1u;
     }
     __syncthreads();
     int8_t *tab = tab_sub + (int64_t)s * NCOARSE;
@@ -329,9 +341,9 @@ __global__ void k_bracket(const float *__restrict__ Yb, const float *__restrict_
 }
 
 cudaError_t launch_bracket(const float *Y, const float *centre, float margin, int S, int K,
-                           int8_t *tab_sub, int32_t *n_sub, cudaStream_t st)
+                           int8_t *tab_sub, int32_t *n_sub, uint32_t *range, cudaStream_t st)
 {
-    k_bracket<<<S, 256, 0, st>>>(Y, centre, margin, K, tab_sub, n_sub);
+    k_bracket<<<S, 256, 0, st>>>(Y, centre, margin, K, tab_sub, n_sub, range);
     return cudaGetLastError();
 }
 

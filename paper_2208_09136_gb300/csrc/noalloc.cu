@@ -40,7 +40,8 @@ constexpr size_t O_TFIN1 = O_TMID + al((size_t)NA_MAX_S * NCOARSE);
 constexpr size_t O_TFIN2 = O_TFIN1 + al((size_t)NA_MAX_S * NCOARSE);
 constexpr size_t O_NGROUPS = O_TFIN2 + al((size_t)NA_MAX_S * KMAX * NFINE);
 constexpr size_t O_RANGE = O_NGROUPS + al(sizeof(int32_t) * 3 * NA_MAX_S);
-constexpr size_t O_HIST = O_RANGE + al(sizeof(uint32_t) * 2 * NA_MAX_S);
+constexpr size_t O_REDO = O_RANGE + al(sizeof(uint32_t) * 2 * NA_MAX_S);
+constexpr size_t O_HIST = O_REDO + 256;
 constexpr size_t NA_BYTES = O_HIST + al(sizeof(uint64_t) * NA_HSTRIDE * NA_MAX_S);
 static_assert(NA_BYTES <= (size_t)RQA_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds its array");
 
@@ -101,6 +102,7 @@ __global__ void k_na_setup(NaPlan pl, unsigned char *scr)
     if (t == 0) *reinterpret_cast<int *>(scr + O_STATUS) = 0;
     if (t < 64) reinterpret_cast<unsigned *>(scr + O_QUEUE)[t] = 0u;
     if (t < 3 * NA_MAX_S) reinterpret_cast<int32_t *>(scr + O_NGROUPS)[t] = 0;
+    if (t < NA_MAX_S) scr[O_REDO + t] = 1;  // the plain coarse round for every series
     for (int s = 0; s < pl.S; ++s) {
         if (t == 0) sd[s] = pl.sd[s];
         if (t < pl.K) T[s * pl.K + t] = pl.T[s][t];
@@ -212,6 +214,7 @@ extern "C" int rqa_eps_for_rr_noalloc(const rqa_batch *b, const int32_t *rr_num,
     sb.n_mid = ng + pl.S;
     sb.n_fin = ng + 2 * pl.S;
     sb.range = reinterpret_cast<uint32_t *>(scr + O_RANGE);
+    sb.redo = scr + O_REDO;
     sb.hist = reinterpret_cast<uint64_t *>(scr + O_HIST);
     sb.hstride = NCOARSE + (int64_t)(K > NSUB_MAX ? K : NSUB_MAX) * NFINE;
 

@@ -56,6 +56,7 @@ struct SelBufs {
     int8_t *tab_fin2;      // [s][KMAX][NFINE] (super group, middle digit) -> group
     int32_t *n_sub, *n_mid, *n_fin;   // [s]
     uint32_t *range;       // [s][2]: keys the next filtered round can count, inclusive
+    uint8_t *redo;         // [s]: 1 = the plain coarse round runs for this series
     uint64_t *hist;        // [s][hstride]: NCOARSE coarse bins then fine bins
     int64_t hstride;
 };

@@ -27,8 +27,9 @@ cudaError_t mlp_backward(const float *params, const float *X, const float *acts,
                          float *loss, float *scratch, cudaStream_t st);
 cudaError_t adam_step(float *p, const float *g, float *m, float *v, int64_t n, int t, float lr,
                       float b1, float b2, float eps, cudaStream_t st);
+// also writes range[2s], range[2s+1]: the keys of the split buckets' span
 cudaError_t launch_bracket(const float *Y, const float *centre, float margin, int S, int K,
-                           int8_t *tab_sub, int32_t *n_sub, cudaStream_t st);
+                           int8_t *tab_sub, int32_t *n_sub, uint32_t *range, cudaStream_t st);
 cudaError_t launch_bracket_stats(const uint8_t *level, int64_t n, unsigned long long *hm,
                                  cudaStream_t st);
 

@@ -70,14 +70,23 @@ __device__ __forceinline__ int bin_of(uint32_t key, const int8_t *t1, const int8
 // One persistent launch over the work items; each CTA histograms the keys of
 // its item's bands in shared memory and adds the non-zero bins to the
 // series' 64-bit global histogram at the end of the item.
+//
+// R_COARSE counts every key.  The other rounds count only keys inside a key
+// range (the split buckets of the bracket, or the groups of the middle and
+// final rounds): a lane keeps the keys of its 16 cells of a row block in
+// registers and marks the ones inside; only when some lane of the warp has a
+// mark does the warp take the counting path.  The bracket round also counts
+// the keys below its range, in a register, as one number.
 template <int ROUND, int M, int TAU>
 __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K)
 {
+    constexpr bool FILTERED = ROUND != R_COARSE;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int slot;
     __shared__ int nb_used_sh;
     __shared__ int next_band;
     __shared__ uint32_t key_lo, key_hi;
+    __shared__ unsigned long long below_sh;
     const int nbins_max = (ROUND == R_COARSE) ? NCOARSE
                         : (ROUND == R_COARSE_SUB) ? NCOARSE + NSUB_MAX * NFINE
                                                   : K * NFINE;
@@ -95,18 +104,19 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
         const SeriesDev sd = a.series[item.s];
         if (threadIdx.x == 0) {
             int nb;
-            if (ROUND == R_COARSE) nb = NCOARSE;
-            else if (ROUND == R_COARSE_SUB) nb = NCOARSE + sb.n_sub[item.s] * NFINE;
+            if (ROUND == R_COARSE) nb = sb.redo[item.s] ? NCOARSE : 0;
+            else if (ROUND == R_COARSE_SUB) nb = sb.n_sub[item.s] ? NCOARSE + sb.n_sub[item.s] * NFINE : 0;
             else if (ROUND == R_MID) nb = sb.n_mid[item.s] * NFINE;
             else nb = sb.n_fin[item.s] * NFINE;
             nb_used_sh = nb;
             next_band = item.b_lo;
             key_lo = 0u;
             key_hi = 0xffffffffu;
-            if (ROUND == R_MID || ROUND == R_FINAL) {
+            if (FILTERED) {
                 key_lo = sb.range[2 * (int64_t)item.s];
                 key_hi = sb.range[2 * (int64_t)item.s + 1];
             }
+            below_sh = 0ull;
         }
         __syncthreads();
         const int nb_used = nb_used_sh;
@@ -124,7 +134,8 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
         }
 
         const float *ys = a.y + sd.off;
-        const uint32_t klo = key_lo, khi = key_hi;
+        const uint32_t klo = key_lo, kspan = key_hi - key_lo;  // inside: key - klo <= kspan
+        uint32_t below = 0;  // bracket round: keys under its range
         for (;;) {
             // bands are handed to warps one at a time, so no warp idles while
             // another still has several bands of the item left
@@ -140,8 +151,6 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
             // one cell's key into the histogram; consecutive cells of a lane
             // are neighbours in the matrix, so equal bins are aggregated
             auto count_key = [&](uint32_t key) {
-                // filtered rounds: most keys fall outside every group
-                if ((ROUND == R_MID || ROUND == R_FINAL) && (key < klo || key > khi)) return;
                 const int bin = bin_of<ROUND>(key, t1, t2);
                 if (bin < 0) return;
                 if (bin == last) {
@@ -152,30 +161,56 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
                     run = 1;
                 }
             };
-            int i0 = 0;
-            // interior row blocks: every lane's cells on all BAND diagonals exist
-            for (; i0 + 32 <= rows - (BAND - 1); i0 += 32) {
-                const int i = i0 + lane;
-                BandTile<M, TAU, BAND> tile;
-                tile.load_fast(ys, i, d_lo, sd.tau);
-#pragma unroll
-                for (int j = 0; j < BAND; ++j)
-                    count_key(__float_as_uint(tile.dist(ys, j, i, d_lo + j, sd.tau, sd.m)));
-            }
-            for (; i0 < rows; i0 += 32) {
-                const int i = i0 + lane;
-                BandTile<M, TAU, BAND> tile;
-                tile.load(ys, sd.n, i, d_lo, rows, sd.tau, sd.m);
+            // the 16 cells of a lane in one row block; valid = inside the triangle
+            auto row_block = [&](const BandTile<M, TAU, BAND> &tile, int i, bool interior) {
+                uint32_t key[BAND];
+                uint32_t mark = 0;
 #pragma unroll
                 for (int j = 0; j < BAND; ++j) {
                     const int dl = d_lo + j;
-                    if (i < sd.ne - dl)
-                        count_key(__float_as_uint(tile.dist(ys, j, i, dl, sd.tau, sd.m)));
+                    const bool valid = interior || i < sd.ne - dl;
+                    key[j] = __float_as_uint(tile.dist(ys, j, i, dl, sd.tau, sd.m));
+                    if (!FILTERED) {
+                        if (valid) count_key(key[j]);
+                    } else {
+                        if (valid && key[j] - klo <= kspan) mark |= 1u << j;
+                        if (ROUND == R_COARSE_SUB) below += (valid && key[j] < klo) ? 1u : 0u;
+                    }
                 }
+                if (FILTERED && __any_sync(FULL, mark != 0)) {
+#pragma unroll
+                    for (int j = 0; j < BAND; ++j)
+                        if (mark & (1u << j)) count_key(key[j]);
+                }
+            };
+            int i0 = 0;
+            // interior row blocks: every lane's cells on all BAND diagonals exist
+            for (; i0 + 32 <= rows - (BAND - 1); i0 += 32) {
+                BandTile<M, TAU, BAND> tile;
+                tile.load_fast(ys, i0 + lane, d_lo, sd.tau);
+                row_block(tile, i0 + lane, true);
+            }
+            for (; i0 < rows; i0 += 32) {
+                BandTile<M, TAU, BAND> tile;
+                tile.load(ys, sd.n, i0 + lane, d_lo, rows, sd.tau, sd.m);
+                row_block(tile, i0 + lane, false);
             }
             if (run) atomicAdd(&h[last], run);
         }
+        if (ROUND == R_COARSE_SUB) {
+            // keys under the bracket: one count, kept in the coarse bucket
+            // just below it (every bucket under it is empty in this round)
+            unsigned long long bw = below;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) bw += __shfl_xor_sync(FULL, bw, o);
+            if (lane == 0 && bw) atomicAdd(&below_sh, bw);
+        }
         __syncthreads();
+        if (ROUND == R_COARSE_SUB && threadIdx.x == 0 && below_sh) {
+            const int cb = (int)(klo >> COARSE_SHIFT) - 1;  // >= 0 whenever keys lie below
+            atomicAdd(reinterpret_cast<unsigned long long *>(sb.hist + (int64_t)item.s * sb.hstride + cb),
+                      below_sh);
+        }
         uint64_t *gh = sb.hist + (int64_t)item.s * sb.hstride + (ROUND >= R_MID ? NCOARSE : 0);
         for (int x = threadIdx.x; x < nb_used; x += THREADS) {
             const uint32_t v = h[x];
@@ -292,7 +327,10 @@ k_select(SelBufs sb, const SeriesDev *series, int s_begin, int K, float *eps_out
     const uint64_t *gfine = gh + NCOARSE;
     (void)series;
 
+    if (ROUND == R_COARSE && !sb.redo[s]) return;  // the bracket settled this series
     if (ROUND == R_COARSE || ROUND == R_COARSE_SUB) {
+        __shared__ int hard;  // bracket round: some target outside the bracket
+        if (t == 0) hard = 0;
         // bucket totals; a split bucket's keys sit in its fine group
         for (int x = t; x < NCOARSE; x += THREADS) cum[x] = gh[x];
         __syncthreads();
@@ -323,10 +361,18 @@ k_select(SelBufs sb, const SeriesDev *series, int s_begin, int K, float *eps_out
             }
         }
         block_scan_u64(cum, NCOARSE, wt);
+        // bracket round: only the bracket's buckets were counted (keys under it
+        // lumped into the bucket just below, keys above it not at all)
+        const int sub_lo = (int)(sb.range[2 * (int64_t)s] >> COARSE_SHIFT);
+        const int sub_hi = (int)(sb.range[2 * (int64_t)s + 1] >> COARSE_SHIFT);
         if (t < K) {
             const uint64_t R = sb.T[sk + t];
             const int c = lower_bound_u64(cum, NCOARSE, R);
-            if (c >= NCOARSE || R == 0) {
+            if (ROUND == R_COARSE_SUB &&
+                (sb.n_sub[s] == 0 || c >= NCOARSE || c < sub_lo || c > sub_hi)) {
+                pre[t] = 0; lev[t] = 0; rnk[t] = R; blw[t] = 0;  // outside: full selection
+                hard = 1;
+            } else if (c >= NCOARSE || R == 0) {
                 set_status(status, 10 /*INTERNAL*/);
                 pre[t] = 0; lev[t] = 1; rnk[t] = 1; blw[t] = 0;
             } else {
@@ -341,7 +387,7 @@ k_select(SelBufs sb, const SeriesDev *series, int s_begin, int K, float *eps_out
         __syncthreads();
         if (ROUND == R_COARSE_SUB) {
             const int8_t *tab = sb.tab_sub + (int64_t)s * NCOARSE;
-            if (t < K) grp[t] = tab[pre[t]];
+            if (t < K) grp[t] = (lev[t] == 1) ? tab[pre[t]] : -1;
             __syncthreads();
             const int nsub = sb.n_sub[s];
             for (int g = 0; g < nsub; ++g) {
@@ -362,6 +408,13 @@ k_select(SelBufs sb, const SeriesDev *series, int s_begin, int K, float *eps_out
                     }
                 }
                 __syncthreads();
+            }
+        }
+        if (ROUND == R_COARSE_SUB) {
+            if (t == 0) sb.redo[s] = (uint8_t)hard;
+            if (hard) {  // the plain rounds redo this series; levels kept for the statistics
+                if (t < K) sb.level[sk + t] = lev[t];
+                return;
             }
         }
         // middle-round table: coarse bucket -> group, for targets at level 1
