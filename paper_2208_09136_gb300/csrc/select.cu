@@ -44,7 +44,7 @@ int count_smem_bytes(int round, int K)
     case R_COARSE: return NCOARSE * 4;
     case R_COARSE_SUB: return (NCOARSE + NSUB_MAX * NFINE) * 4 + NCOARSE;
     case R_MID: return K * NFINE * 4 + NCOARSE;
-    default: return K * NFINE * 4 + NCOARSE + K * NFINE;
+    default: return NCOARSE + K * NFINE;  // tables only: final-round keys are rare
     }
 }
 
@@ -81,6 +81,8 @@ template <int ROUND, int M, int TAU>
 __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K)
 {
     constexpr bool FILTERED = ROUND != R_COARSE;
+    constexpr bool GATED = ROUND == R_MID || ROUND == R_FINAL;  // few keys inside the range
+    constexpr bool GLOBAL_BINS = ROUND == R_FINAL;             // ... so rare they go to HBM
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int slot;
     __shared__ int nb_used_sh;
@@ -89,7 +91,7 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
     __shared__ unsigned long long below_sh;
     const int nbins_max = (ROUND == R_COARSE) ? NCOARSE
                         : (ROUND == R_COARSE_SUB) ? NCOARSE + NSUB_MAX * NFINE
-                                                  : K * NFINE;
+                        : (ROUND == R_MID) ? K * NFINE : 0;
     uint32_t *h = reinterpret_cast<uint32_t *>(smem);
     int8_t *t1 = reinterpret_cast<int8_t *>(h + nbins_max);
     int8_t *t2 = t1 + NCOARSE;
@@ -135,6 +137,8 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
 
         const float *ys = a.y + sd.off;
         const uint32_t klo = key_lo, kspan = key_hi - key_lo;  // inside: key - klo <= kspan
+        unsigned long long *gbins =
+            reinterpret_cast<unsigned long long *>(sb.hist + (int64_t)item.s * sb.hstride + NCOARSE);
         uint32_t below = 0;  // bracket round: keys under its range
         for (;;) {
             // bands are handed to warps one at a time, so no warp idles while
@@ -153,6 +157,10 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
             auto count_key = [&](uint32_t key) {
                 const int bin = bin_of<ROUND>(key, t1, t2);
                 if (bin < 0) return;
+                if (GLOBAL_BINS) {
+                    atomicAdd(gbins + bin, 1ull);
+                    return;
+                }
                 if (bin == last) {
                     ++run;
                 } else {
@@ -172,12 +180,16 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
                     key[j] = __float_as_uint(tile.dist(ys, j, i, dl, sd.tau, sd.m));
                     if (!FILTERED) {
                         if (valid) count_key(key[j]);
+                    } else if (!GATED) {  // bracket round: a quarter of the keys are inside
+                        if (valid) {
+                            if (key[j] < klo) ++below;
+                            else if (key[j] - klo <= kspan) count_key(key[j]);
+                        }
                     } else {
                         if (valid && key[j] - klo <= kspan) mark |= 1u << j;
-                        if (ROUND == R_COARSE_SUB) below += (valid && key[j] < klo) ? 1u : 0u;
                     }
                 }
-                if (FILTERED && __any_sync(FULL, mark != 0)) {
+                if (GATED && __any_sync(FULL, mark != 0)) {
 #pragma unroll
                     for (int j = 0; j < BAND; ++j)
                         if (mark & (1u << j)) count_key(key[j]);
@@ -212,7 +224,7 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
                       below_sh);
         }
         uint64_t *gh = sb.hist + (int64_t)item.s * sb.hstride + (ROUND >= R_MID ? NCOARSE : 0);
-        for (int x = threadIdx.x; x < nb_used; x += THREADS) {
+        for (int x = threadIdx.x; x < (GLOBAL_BINS ? 0 : nb_used); x += THREADS) {
             const uint32_t v = h[x];
             if (v) {
                 atomicAdd(reinterpret_cast<unsigned long long *>(gh + x), (unsigned long long)v);
