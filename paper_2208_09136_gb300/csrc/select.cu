@@ -44,7 +44,7 @@ int count_smem_bytes(int round, int K)
     case R_COARSE: return NCOARSE * 4;
     case R_COARSE_SUB: return (NCOARSE + NSUB_MAX * NFINE) * 4 + NCOARSE;
     case R_MID: return K * NFINE * 4 + NCOARSE;
-    default: return NCOARSE + K * NFINE;  // tables only: final-round keys are rare
+    default: return NCOARSE + 1 + K * NFINE;  // tables only: final-round keys are rare
     }
 }
 
@@ -61,9 +61,10 @@ __device__ __forceinline__ int bin_of(uint32_t key, const int8_t *t1, const int8
         int g = t1[key >> COARSE_SHIFT];
         return g < 0 ? -1 : g * NFINE + (int)((key >> 10) & (NFINE - 1));
     }
-    int g1 = t1[key >> COARSE_SHIFT];
-    if (g1 < 0) return -1;
-    int g = t2[g1 * NFINE + (int)((key >> 10) & (NFINE - 1))];
+    // t2[0] is a -1 sentinel: no branch on the first lookup
+    const int g1 = t1[key >> COARSE_SHIFT];
+    const int idx = g1 < 0 ? 0 : 1 + g1 * NFINE + (int)((key >> 10) & (NFINE - 1));
+    const int g = t2[idx];
     return g < 0 ? -1 : g * NFINE + (int)(key & (NFINE - 1));
 }
 
@@ -71,18 +72,15 @@ __device__ __forceinline__ int bin_of(uint32_t key, const int8_t *t1, const int8
 // its item's bands in shared memory and adds the non-zero bins to the
 // series' 64-bit global histogram at the end of the item.
 //
-// R_COARSE counts every key.  The other rounds count only keys inside a key
-// range (the split buckets of the bracket, or the groups of the middle and
-// final rounds): a lane keeps the keys of its 16 cells of a row block in
-// registers and marks the ones inside; only when some lane of the warp has a
-// mark does the warp take the counting path.  The bracket round also counts
-// the keys below its range, in a register, as one number.
+// R_COARSE counts every key.  The bracket round counts only the keys of its
+// split range and keeps the keys below it as one register count; the middle
+// and final rounds look each key up in their group tables (the final round's
+// rare hits go straight to the global bins, so it needs no shared histogram).
 template <int ROUND, int M, int TAU>
 __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K)
 {
     constexpr bool FILTERED = ROUND != R_COARSE;
-    constexpr bool GATED = ROUND == R_MID || ROUND == R_FINAL;  // few keys inside the range
-    constexpr bool GLOBAL_BINS = ROUND == R_FINAL;             // ... so rare they go to HBM
+    constexpr bool GLOBAL_BINS = ROUND == R_FINAL;  // final-round keys are rare: count in HBM
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int slot;
     __shared__ int nb_used_sh;
@@ -130,7 +128,8 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
             for (int x = threadIdx.x; x < NCOARSE; x += THREADS) t1[x] = src[x];
             if (ROUND == R_FINAL) {
                 const int8_t *s2 = sb.tab_fin2 + (int64_t)item.s * KMAX * NFINE;
-                for (int x = threadIdx.x; x < K * NFINE; x += THREADS) t2[x] = s2[x];
+                for (int x = threadIdx.x; x < K * NFINE; x += THREADS) t2[1 + x] = s2[x];
+                if (threadIdx.x == 0) t2[0] = -1;
             }
             __syncthreads();
         }
@@ -171,28 +170,19 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
             };
             // the 16 cells of a lane in one row block; valid = inside the triangle
             auto row_block = [&](const BandTile<M, TAU, BAND> &tile, int i, bool interior) {
-                uint32_t key[BAND];
-                uint32_t mark = 0;
 #pragma unroll
                 for (int j = 0; j < BAND; ++j) {
                     const int dl = d_lo + j;
                     const bool valid = interior || i < sd.ne - dl;
-                    key[j] = __float_as_uint(tile.dist(ys, j, i, dl, sd.tau, sd.m));
-                    if (!FILTERED) {
-                        if (valid) count_key(key[j]);
-                    } else if (!GATED) {  // bracket round: a quarter of the keys are inside
+                    const uint32_t key = __float_as_uint(tile.dist(ys, j, i, dl, sd.tau, sd.m));
+                    if (ROUND == R_COARSE_SUB) {  // a quarter of the keys are inside the bracket
                         if (valid) {
-                            if (key[j] < klo) ++below;
-                            else if (key[j] - klo <= kspan) count_key(key[j]);
+                            if (key < klo) ++below;
+                            else if (key - klo <= kspan) count_key(key);
                         }
-                    } else {
-                        if (valid && key[j] - klo <= kspan) mark |= 1u << j;
+                    } else if (valid) {
+                        count_key(key);
                     }
-                }
-                if (GATED && __any_sync(FULL, mark != 0)) {
-#pragma unroll
-                    for (int j = 0; j < BAND; ++j)
-                        if (mark & (1u << j)) count_key(key[j]);
                 }
             };
             int i0 = 0;
