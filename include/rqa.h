@@ -85,8 +85,8 @@ typedef struct {
     int schedule;      /* RQA_SCHED_* */
     int select;        /* RQA_SELECT_* */
     int band;          /* diagonals per warp band of the line pass: 0 = default
-                          (8), else 4, 8 or 16 (4 and 16 only for (m, tau) =
-                          (1, any), (3, 1), (3, 3); otherwise 8 is used) */
+                          (4), else 4, 8 or 16 (8 and 16 only for (m, tau) =
+                          (1, any), (3, 1), (3, 3); otherwise 4 is used) */
     int blocks_per_sm; /* persistent CTAs per SM: 0 = as many as each kernel
                           can keep resident, else at most this many */
     int reserved[4];   /* must be zero */

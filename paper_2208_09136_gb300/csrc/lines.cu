@@ -17,6 +17,7 @@
 // P_k(l) for l <= LSH in shared memory (flushed once per work item), longer
 // lines straight to the caller's full histogram, and L_max.
 #include <cstdint>
+#include <type_traits>
 #include "rqa_common.cuh"
 
 namespace rqa {
@@ -26,24 +27,25 @@ template <bool HIST>
 struct LineSink {
     uint32_t *hs;           // this lane's column of the warp's shared histogram, [length][lane]
     uint64_t *hist;         // this series' full histogram row for lane k, or null
-    uint32_t lmax;
+    uint32_t lmax;          // longest line over LSH (shorter ones: read from hs at flush)
     uint32_t c1, c2, c3;    // interior lines of length 1, 2, 3, counted by popcount
     bool real;              // lane < K (the other lanes write a dummy row)
     // one line of length len; len == 0 means none (slot 0 is a scratch slot)
     __device__ __forceinline__ void emit(uint32_t len)
     {
         hs[(len <= (uint32_t)LSH ? len : 0u) * 32u] += 1u;  // own column: own bank
-        if (HIST && len > (uint32_t)LSH && real)
-            atomicAdd(reinterpret_cast<unsigned long long *>(hist + (len - 1)), 1ull);
-        lmax = max(lmax, len);
+        if (len > (uint32_t)LSH) {  // rare
+            if (HIST && real)
+                atomicAdd(reinterpret_cast<unsigned long long *>(hist + (len - 1)), 1ull);
+            lmax = max(lmax, len);
+        }
     }
-    // fold the popcount tallies into the histogram row
+    // fold the popcount tallies into the histogram column
     __device__ __forceinline__ void settle()
     {
         hs[1 * 32] += c1;
         hs[2 * 32] += c2;
         hs[3 * 32] += c3;
-        lmax = max(lmax, c3 ? 3u : c2 ? 2u : c1 ? 1u : 0u);
         c1 = c2 = c3 = 0;
     }
 };
@@ -112,7 +114,7 @@ __device__ __forceinline__ void unit_of(const CellArgs &a, int64_t u, int &s, in
 // its own histogram in shared memory, flushed when it moves to another series
 // and at exit.  No CTA-wide barrier, so no warp waits for another.
 template <int D, int M, int TAU, bool HIST>
-__global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int K)
+__global__ void __launch_bounds__(THREADS, 2) k_lines(CellArgs a, LineBufs lb, int K)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -145,8 +147,21 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
 
     auto flush = [&]() {
         if (cur < 0) return;
+        if (klane) sink.settle();
+        __syncwarp();
+        uint64_t *gs = lb.hshort + ((int64_t)cur * K + lane) * LSH;
+        uint32_t lm = sink.lmax;
+#pragma unroll 1
+        for (int l = 1; l <= LSH; ++l) {  // row l: one bank per lane
+            const uint32_t v = hs[l * 32 + lane];
+            if (klane && v) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(gs + (l - 1)), (unsigned long long)v);
+                hs[l * 32 + lane] = 0;
+                lm = max(lm, (uint32_t)l);
+            }
+        }
+        sink.lmax = lm;
         if (klane) {
-            sink.settle();
             const int64_t o = (int64_t)cur * K + lane;
             if (cnt) atomicAdd(reinterpret_cast<unsigned long long *>(lb.count + o),
                                (unsigned long long)cnt);
@@ -155,16 +170,6 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
         cnt = 0;
         sink.lmax = 0;
         sink.c1 = sink.c2 = sink.c3 = 0;
-        __syncwarp();
-        uint64_t *gs = lb.hshort + ((int64_t)cur * K + lane) * LSH;
-#pragma unroll 1
-        for (int l = 1; l <= LSH; ++l) {  // row l: one bank per lane
-            const uint32_t v = hs[l * 32 + lane];
-            if (klane && v) {
-                atomicAdd(reinterpret_cast<unsigned long long *>(gs + (l - 1)), (unsigned long long)v);
-                hs[l * 32 + lane] = 0;
-            }
-        }
         __syncwarp();
     };
 
@@ -231,61 +236,73 @@ __global__ void __launch_bounds__(THREADS) k_lines(CellArgs a, LineBufs lb, int 
         if (bad) continue;
 
         const float *ys = a.y + sd.off;
-        for (int b = ub_lo; b < ub_hi; ++b) {
-        int d_lo, d_hi;
-        band_range(b, D, sd.ne, d_lo, d_hi);
-        const int rows = sd.ne - d_lo;
-        uint32_t carry[D];
+        // the unit's bands; the rank method is fixed per unit (branch hoisted)
+        auto bands = [&](auto use_table) {
+            constexpr bool TABLE = decltype(use_table)::value;
+            for (int b = ub_lo; b < ub_hi; ++b) {
+                int d_lo, d_hi;
+                band_range(b, D, sd.ne, d_lo, d_hi);
+                const int rows = sd.ne - d_lo;
+                uint32_t carry[D];
 #pragma unroll
-        for (int j = 0; j < D; ++j) carry[j] = 0;
-        for (int i0 = 0; i0 < rows; i0 += 32) {
-            const int i = i0 + lane;
-            BandTile<M, TAU, D> tile;
-            tile.load(ys, sd.n, i, d_lo, rows, sd.tau, sd.m);
+                for (int j = 0; j < D; ++j) carry[j] = 0;
+                for (int i0 = 0; i0 < rows; i0 += 32) {
+                    const int i = i0 + lane;
+                    BandTile<M, TAU, D> tile;
+                    tile.load(ys, sd.n, i, d_lo, rows, sd.tau, sd.m);
 #pragma unroll
-            for (int j = 0; j < D; ++j) {
-                const int dl = d_lo + j;
-                uint32_t r = 31;  // outside the diagonal: recurrent for no k
-                if (i < sd.ne - dl) {
-                    const uint32_t key = __float_as_uint(tile.dist(ys, j, i, dl, sd.tau, sd.m));
-                    if (use_tab) {
-                        const int q = min(max((int)(key >> tshift) - tbase, -1), tnb) + 1;
-                        const uint32_t e = tab[q];
-                        r = (e & 31u) + (((key & tmask) > (e >> 11)) ? ((e >> 5) & 63u) : 0u);
-                    } else {
-                        r = 0;
-                        r += (epsb[r + 15] < key) ? 16u : 0u;
-                        r += (epsb[r + 7] < key) ? 8u : 0u;
-                        r += (epsb[r + 3] < key) ? 4u : 0u;
-                        r += (epsb[r + 1] < key) ? 2u : 0u;
-                        r += (epsb[r] < key) ? 1u : 0u;
+                    for (int j = 0; j < D; ++j) {
+                        const int dl = d_lo + j;
+                        const bool valid = i < sd.ne - dl;
+                        uint32_t r = 31;  // outside the diagonal: recurrent for no k
+                        // register windows read no memory per cell, so cells
+                        // outside the triangle are computed and discarded
+                        if (TAU > 0 || valid) {
+                            const uint32_t key =
+                                __float_as_uint(tile.dist(ys, j, i, dl, sd.tau, sd.m));
+                            uint32_t rk;
+                            if (TABLE) {
+                                const int q = min(max((int)(key >> tshift) - tbase, -1), tnb) + 1;
+                                const uint32_t e = tab[q];
+                                rk = (e & 31u) + (((key & tmask) > (e >> 11)) ? ((e >> 5) & 63u) : 0u);
+                            } else {
+                                rk = 0;
+                                rk += (epsb[rk + 15] < key) ? 16u : 0u;
+                                rk += (epsb[rk + 7] < key) ? 8u : 0u;
+                                rk += (epsb[rk + 3] < key) ? 4u : 0u;
+                                rk += (epsb[rk + 1] < key) ? 2u : 0u;
+                                rk += (epsb[rk] < key) ? 1u : 0u;
+                            }
+                            r = valid ? rk : 31u;
+                        }
+                        const uint32_t B0 = __ballot_sync(FULL, r & 1u);
+                        const uint32_t B1 = __ballot_sync(FULL, r & 2u);
+                        const uint32_t B2 = __ballot_sync(FULL, r & 4u);
+                        const uint32_t B3 = __ballot_sync(FULL, r & 8u);
+                        const uint32_t B4 = __ballot_sync(FULL, r & 16u);
+                        // lane k's word {t : r_t <= k}; gt = {t : r_t > k}, most
+                        // significant bit plane first.  Lanes >= K run the same
+                        // code on their scratch column, so the warp never diverges.
+                        uint32_t gt = B4 & ~km[4];
+                        uint32_t eq = ~(B4 ^ km[4]);
+                        gt |= eq & B3 & ~km[3];
+                        eq &= ~(B3 ^ km[3]);
+                        gt |= eq & B2 & ~km[2];
+                        eq &= ~(B2 ^ km[2]);
+                        gt |= eq & B1 & ~km[1];
+                        eq &= ~(B1 ^ km[1]);
+                        gt |= eq & B0 & ~km[0];
+                        const uint32_t w = ~gt;
+                        cnt += __popc(w);
+                        runs_word(w, carry[j], sink);
                     }
                 }
-                const uint32_t B0 = __ballot_sync(FULL, r & 1u);
-                const uint32_t B1 = __ballot_sync(FULL, r & 2u);
-                const uint32_t B2 = __ballot_sync(FULL, r & 4u);
-                const uint32_t B3 = __ballot_sync(FULL, r & 8u);
-                const uint32_t B4 = __ballot_sync(FULL, r & 16u);
-                // lane k's word {t : r_t <= k}; gt = {t : r_t > k}, most
-                // significant bit plane first.  Lanes >= K run the same code
-                // on their scratch row, so the warp never diverges here.
-                uint32_t gt = B4 & ~km[4];
-                uint32_t eq = ~(B4 ^ km[4]);
-                gt |= eq & B3 & ~km[3];
-                eq &= ~(B3 ^ km[3]);
-                gt |= eq & B2 & ~km[2];
-                eq &= ~(B2 ^ km[2]);
-                gt |= eq & B1 & ~km[1];
-                eq &= ~(B1 ^ km[1]);
-                gt |= eq & B0 & ~km[0];
-                const uint32_t w = ~gt;
-                cnt += __popc(w);
-                runs_word(w, carry[j], sink);
-            }
-        }
 #pragma unroll
-        for (int j = 0; j < D; ++j) sink.emit(carry[j]);  // lines reaching the diagonal's end
-        }  // bands of the unit
+                for (int j = 0; j < D; ++j) sink.emit(carry[j]);  // lines reaching the diagonal's end
+            }
+        };
+        if (use_tab) bands(std::true_type{});
+        else bands(std::false_type{});
         // flush after each unit: a warp's next unit is usually another series
         flush();
         cur = -1;
@@ -309,10 +326,10 @@ static cudaError_t launch_lines_h(const CellArgs &a, const LineBufs &lb, int K, 
                                   int embed, cudaStream_t st)
 {
     void (*kern)(CellArgs, LineBufs, int) = nullptr;
-    switch (a.band_lines) {  // band width: specialised embeddings only, others use 8
-    case 4: kern = lines_kernel_d<4, HIST>(embed); break;
+    switch (a.band_lines) {  // band width: specialised embeddings only, others use 4
+    case 8: kern = lines_kernel_d<8, HIST>(embed); break;
     case 16: kern = lines_kernel_d<16, HIST>(embed); break;
-    default: kern = lines_kernel_d<8, HIST>(embed); break;
+    default: kern = lines_kernel_d<4, HIST>(embed); break;
     }
     if (!kern) {
         if (a.band_lines != DL_DEFAULT) return cudaErrorInvalidValue;
@@ -337,7 +354,7 @@ bool lines_band_ok(int embed, int band)
 {
     if (band == DL_DEFAULT) return true;
     const bool special = embed == E_M1T1 || embed == E_M3T1 || embed == E_M3T3;
-    return special && (band == 4 || band == 16);
+    return special && (band == 8 || band == 16);
 }
 
 cudaError_t launch_lines(const CellArgs &a, const LineBufs &lb, int K, int grid, int embed,

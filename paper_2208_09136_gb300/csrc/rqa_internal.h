@@ -18,7 +18,7 @@ constexpr int LSH = 64;            // line lengths 1..LSH counted in shared memo
 constexpr int LMIN_MAX = 8;        // entries of an lmin list
 constexpr int THREADS = 256;       // threads per CTA of the cell kernels
 constexpr int BAND = 16;           // diagonals per warp band of the counting rounds
-constexpr int DL_DEFAULT = 8;      // diagonals per warp band of the line pass
+constexpr int DL_DEFAULT = 4;      // diagonals per warp band of the line pass
 constexpr int WARPS = THREADS / 32;
 
 // Counting rounds of the selection.
