@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--cpu-cells", type=float, default=1.2e8,
                     help="cells of the oracle's bounded sample")
     ap.add_argument("--band", type=int, default=0, help="line-pass band width (0 = default)")
+    ap.add_argument("--select", default="auto", choices=["auto", "radix"],
+                    help="auto: learned bracket when a model file exists")
     return ap.parse_args()
 
 
@@ -187,6 +189,22 @@ def run_oracle(flat, offsets, m, tau, pick):
     return time.perf_counter() - t0
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """Largest value of x over the ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(cells_per_rank: int, world: int, ms_max: float) -> float:
+    """Weak scaling: every rank processes its own copy of the workload, the job
+    finishes with the slowest rank."""
+    return world * cells_per_rank / (ms_max * 1e-3)
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -251,7 +269,7 @@ def main():
     S, K = len(offsets) - 1, len(RR)
     form = args.form
     from paper_2208_09136_gb300 import bracket
-    have_model = os.path.exists(bracket.MODEL_PATH) and form != "plain"
+    have_model = os.path.exists(bracket.MODEL_PATH) and form != "plain" and args.select == "auto"
     if form == "auto":
         form = "batched"
     stream = torch.cuda.Stream(device=dev)
@@ -321,12 +339,8 @@ def main():
         raise SystemExit(f"device error: {rqa.rqa_error_string(code)}")
     phase /= args.steps
 
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * total_cells / (ms_max * 1e-3)
+    ms_max = max_over_ranks(ms, dist, dev)
+    value = whole_job_rate(total_cells, world, ms_max)
     series_per_s = world * S / (ms_max * 1e-3)
 
     # plain per-series form of the same step, for comparison
@@ -382,12 +396,8 @@ def main():
             stream.synchronize()
             if i > 0:
                 tot += e0.elapsed_time(e1)
-        ems = tot / n_e2e
-        if dist is not None:
-            t = torch.tensor([ems], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * total_cells / (ems * 1e-3), "unit": UNIT,
+        ems = max_over_ranks(tot / n_e2e, dist, dev)
+        e2e = {"value": whole_job_rate(total_cells, world, ems), "unit": UNIT,
                "h2d_bytes_per_step": int(h_y.numel() * 4),
                "d2h_bytes_per_step": int((h_avg.numel() + h_det.numel()) * 8 + h_eps.numel() * 4),
                "ms_per_step": ems, "note": "series H2D, DET/avg DET/eps D2H; P(l) stays on device"}
