@@ -59,12 +59,13 @@ struct LineSink {
 template <class Sink>
 __device__ __forceinline__ void runs_word(uint32_t w, uint32_t &c, Sink &sink)
 {
-    const bool full = (w == FULL);
     const uint32_t nw = ~w;
-    const uint32_t t0 = full ? 0u : (uint32_t)(__ffs(nw) - 1);  // low ones
-    const uint32_t tl = full ? 0u : (uint32_t)__clz(nw);        // high ones
-    sink.emit(full ? 0u : c + t0);
-    const uint32_t mid = full ? 0u : (w & (FULL << t0) & (FULL >> tl));
+    const uint32_t t0 = __clz(__brev(nw));  // low ones; 32 for a full word
+    const uint32_t tl = __clz(nw);          // high ones; 32 for a full word
+    const bool open = t0 == 32u;            // the carried run crosses the whole word
+    sink.emit(open ? 0u : c + t0);
+    // interior: drop the low and the high ones (clamped shifts give 0 at 32)
+    const uint32_t mid = w & __funnelshift_lc(0u, FULL, t0) & __funnelshift_rc(FULL, 0u, tl);
     const uint32_t st = mid & ~(mid << 1);   // first cell of each interior line
     const uint32_t s2 = st & (mid >> 1);     // ... of lines of length >= 2
     const uint32_t s3 = s2 & (mid >> 2);     // >= 3
@@ -78,12 +79,13 @@ __device__ __forceinline__ void runs_word(uint32_t w, uint32_t &c, Sink &sink)
         sink.emit((uint32_t)(__ffs(~(mid >> p)) - 1));
         x &= x - 1;
     }
-    c = full ? c + 32u : tl;
+    c = open ? c + 32u : tl;
 }
 
 // Rank table: keys bucketed by key >> shift, at most one distinct threshold
-// per bucket; entry = rank at the bucket start (bits 0-4), thresholds in the
-// bucket (bits 5-10) and their key's offset inside the bucket (bits 11-31).
+// value per bucket; entry = rank of a key up to that value (bits 0-4), rank
+// of a key above it (bits 5-9), and the value's offset inside the bucket
+// (bits 10-31, so shift <= 22).
 constexpr int TMAX = 512;
 
 // Per-warp shared memory: the warp's own short-line histogram laid out
@@ -123,10 +125,11 @@ __global__ void __launch_bounds__(THREADS, 2) k_lines(CellArgs a, LineBufs lb, i
     uint32_t *tab = epsb + 32;
     const bool klane = lane < K;
 
-    // lane k's bits as masks, for the bit-sliced test r <= k
-    uint32_t km[5];
+    // bits of k+1 as masks, for the bit-sliced test r <= k (k = lane <= 30
+    // for real thresholds; lane 31 would need a sixth bit and is scratch)
+    uint32_t kb[5];
 #pragma unroll
-    for (int b = 0; b < 5; ++b) km[b] = ((lane >> b) & 1) ? FULL : 0u;
+    for (int b = 0; b < 5; ++b) kb[b] = (((lane + 1) >> b) & 1) ? FULL : 0u;
 
     for (int x = lane; x < (LSH + 1) * 32; x += 32) hs[x] = 0;
     __syncwarp();
@@ -134,14 +137,14 @@ __global__ void __launch_bounds__(THREADS, 2) k_lines(CellArgs a, LineBufs lb, i
     int cur = -1;
     bool bad = false;
     SeriesDev sd{};
-    uint64_t cnt = 0;
+    uint32_t cnt = 0;  // recurrent cells of the lane's threshold in this unit
     LineSink<HIST> sink;
     sink.hs = hs + lane;
     sink.hist = nullptr;
     sink.lmax = 0;
     sink.c1 = sink.c2 = sink.c3 = 0;
     sink.real = klane;
-    int tshift = 0, tbase = 0, tnb = 0;
+    int tshift = 0, tbase = 0, tbm1 = 0, tnb = 0;
     uint32_t tmask = 0;
     bool use_tab = false;
 
@@ -198,13 +201,14 @@ __global__ void __launch_bounds__(THREADS, 2) k_lines(CellArgs a, LineBufs lb, i
             if (bad && lane == 0) set_status(a.status, 8 /*UNSORTED*/);
             // rank table: the widest buckets that still separate every pair
             // of distinct thresholds
-            tshift = 21;
+            tshift = 22;
             for (; tshift > 0; --tshift) {
                 const bool clash = klane && lane > 0 && prev != v && (prev >> tshift) == (v >> tshift);
                 if (!__any_sync(FULL, clash)) break;
             }
             const uint32_t vmin = __shfl_sync(FULL, v, 0), vmax = __shfl_sync(FULL, v, K - 1);
             tbase = (int)(vmin >> tshift);
+            tbm1 = tbase - 1;
             tnb = (int)(vmax >> tshift) - tbase + 1;
             tmask = (1u << tshift) - 1u;
             use_tab = !bad && tnb + 2 <= TMAX;
@@ -215,7 +219,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_lines(CellArgs a, LineBufs lb, i
                     if (q == 0) {
                         e = 0u;                    // below every threshold's bucket
                     } else if (q == tnb + 1) {
-                        e = (uint32_t)K;           // above: all K thresholds are smaller
+                        e = (uint32_t)K | ((uint32_t)K << 5);  // above: all K thresholds are smaller
                     } else {
                         uint32_t rlo = 0, cnt = 0, off = 0;
                         for (int k = 0; k < K; ++k) {
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_lines(CellArgs a, LineBufs lb, i
                             if (eb < q - 1) ++rlo;
                             else if (eb == q - 1) { ++cnt; off = ek & tmask; }
                         }
-                        e = rlo | (cnt << 5) | (off << 11);
+                        e = rlo | ((rlo + cnt) << 5) | (off << 10);
                     }
                     tab[q] = e;
                 }
@@ -262,9 +266,9 @@ __global__ void __launch_bounds__(THREADS, 2) k_lines(CellArgs a, LineBufs lb, i
                                 __float_as_uint(tile.dist(ys, j, i, dl, sd.tau, sd.m));
                             uint32_t rk;
                             if (TABLE) {
-                                const int q = min(max((int)(key >> tshift) - tbase, -1), tnb) + 1;
+                                const int q = min(max((int)(key >> tshift) - tbm1, 0), tnb + 1);
                                 const uint32_t e = tab[q];
-                                rk = (e & 31u) + (((key & tmask) > (e >> 11)) ? ((e >> 5) & 63u) : 0u);
+                                rk = (((key & tmask) > (e >> 10)) ? (e >> 5) : e) & 31u;
                             } else {
                                 rk = 0;
                                 rk += (epsb[rk + 15] < key) ? 16u : 0u;
@@ -280,19 +284,15 @@ __global__ void __launch_bounds__(THREADS, 2) k_lines(CellArgs a, LineBufs lb, i
                         const uint32_t B2 = __ballot_sync(FULL, r & 4u);
                         const uint32_t B3 = __ballot_sync(FULL, r & 8u);
                         const uint32_t B4 = __ballot_sync(FULL, r & 16u);
-                        // lane k's word {t : r_t <= k}; gt = {t : r_t > k}, most
-                        // significant bit plane first.  Lanes >= K run the same
-                        // code on their scratch column, so the warp never diverges.
-                        uint32_t gt = B4 & ~km[4];
-                        uint32_t eq = ~(B4 ^ km[4]);
-                        gt |= eq & B3 & ~km[3];
-                        eq &= ~(B3 ^ km[3]);
-                        gt |= eq & B2 & ~km[2];
-                        eq &= ~(B2 ^ km[2]);
-                        gt |= eq & B1 & ~km[1];
-                        eq &= ~(B1 ^ km[1]);
-                        gt |= eq & B0 & ~km[0];
-                        const uint32_t w = ~gt;
+                        // lane k's word {t : r_t <= k}: the borrow out of
+                        // r - (k+1), rippled through the five bit planes; each
+                        // step is the 3-input majority (~B_j, kb_j, borrow), one
+                        // LOP3.  Lanes >= K run it on their scratch column.
+                        uint32_t w = ~B0 & kb[0];
+                        w = (~B1 & kb[1]) | (~B1 & w) | (kb[1] & w);
+                        w = (~B2 & kb[2]) | (~B2 & w) | (kb[2] & w);
+                        w = (~B3 & kb[3]) | (~B3 & w) | (kb[3] & w);
+                        w = (~B4 & kb[4]) | (~B4 & w) | (kb[4] & w);
                         cnt += __popc(w);
                         runs_word(w, carry[j], sink);
                     }
