@@ -56,20 +56,43 @@ struct LineSink {
 // high ones stay open.  Lines strictly inside the word are bounded by zeros:
 // those of length 1..3 are counted with popcounts of the run-start mask,
 // longer ones are read one by one with __ffs.
+// 3-input bitwise function with an 8-bit truth table (one LOP3 instruction):
+// bit i of the table is the output for (a, b, c) = bits of (0xF0, 0xCC, 0xAA).
+template <uint32_t LUT>
+__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+    return d;
+}
+constexpr uint32_t LUT_BORROW = 0x8E;      // (~a & b) | (~a & c) | (b & c)
+constexpr uint32_t LUT_A_ANDNOT_B_AND_C = 0x20;  // a & ~b & c
+constexpr uint32_t LUT_NOT_A_AND_B = 0x0C;  // ~a & b (c ignored)
+
+__device__ __forceinline__ uint32_t shr_clamped(uint32_t a, uint32_t n)
+{
+    uint32_t d;  // PTX shr: shift amounts >= 32 give 0
+    asm("shr.b32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(n));
+    return d;
+}
+
 template <class Sink>
 __device__ __forceinline__ void runs_word(uint32_t w, uint32_t &c, Sink &sink)
 {
-    const uint32_t nw = ~w;
-    const uint32_t t0 = __clz(__brev(nw));  // low ones; 32 for a full word
-    const uint32_t tl = __clz(nw);          // high ones; 32 for a full word
-    const bool open = t0 == 32u;            // the carried run crosses the whole word
-    sink.emit(open ? 0u : c + t0);
-    // interior: drop the low and the high ones (clamped shifts give 0 at 32)
-    const uint32_t mid = w & __funnelshift_lc(0u, FULL, t0) & __funnelshift_rc(FULL, 0u, tl);
-    const uint32_t st = mid & ~(mid << 1);   // first cell of each interior line
-    const uint32_t s2 = st & (mid >> 1);     // ... of lines of length >= 2
-    const uint32_t s3 = s2 & (mid >> 2);     // >= 3
-    uint32_t x = s3 & (mid >> 3);            // >= 4
+    const uint32_t low = lop3<LUT_NOT_A_AND_B>(w, w + 1u, 0u);  // lowest zero of w (0 if none)
+    const uint32_t below = low - 1u;             // the low ones; all ones for a full word
+    const uint32_t t0 = __popc(below);           // count of low ones, 32 for a full word
+    const uint32_t tl = __clz(~w);               // high ones (32 for a full word)
+    const bool open = low == 0u;                 // the carried run crosses the whole word
+    const uint32_t ct = c + t0;
+    sink.emit(open ? 0u : ct);                   // the carried run closes at the first zero
+    c = open ? ct : tl;                          // ... and the high ones stay open
+    // interior: without the low ones and without the high ones
+    const uint32_t mid = lop3<LUT_A_ANDNOT_B_AND_C>(w, below, shr_clamped(FULL, tl));
+    const uint32_t st = mid & ~(mid << 1);       // first cell of each interior line
+    const uint32_t s2 = st & (mid >> 1);         // ... of lines of length >= 2
+    const uint32_t s3 = s2 & (mid >> 2);         // >= 3
+    uint32_t x = s3 & (mid >> 3);                // >= 4
     const uint32_t n1 = __popc(st), n2 = __popc(s2), n3 = __popc(s3);
     sink.c1 += n1 - n2;
     sink.c2 += n2 - n3;
@@ -79,7 +102,6 @@ __device__ __forceinline__ void runs_word(uint32_t w, uint32_t &c, Sink &sink)
         sink.emit((uint32_t)(__ffs(~(mid >> p)) - 1));
         x &= x - 1;
     }
-    c = open ? c + 32u : tl;
 }
 
 // Rank table: keys bucketed by key >> shift, at most one distinct threshold
@@ -288,11 +310,11 @@ __global__ void __launch_bounds__(THREADS, 2) k_lines(CellArgs a, LineBufs lb, i
                         // r - (k+1), rippled through the five bit planes; each
                         // step is the 3-input majority (~B_j, kb_j, borrow), one
                         // LOP3.  Lanes >= K run it on their scratch column.
-                        uint32_t w = ~B0 & kb[0];
-                        w = (~B1 & kb[1]) | (~B1 & w) | (kb[1] & w);
-                        w = (~B2 & kb[2]) | (~B2 & w) | (kb[2] & w);
-                        w = (~B3 & kb[3]) | (~B3 & w) | (kb[3] & w);
-                        w = (~B4 & kb[4]) | (~B4 & w) | (kb[4] & w);
+                        uint32_t w = lop3<LUT_NOT_A_AND_B>(B0, kb[0], 0u);
+                        w = lop3<LUT_BORROW>(B1, kb[1], w);
+                        w = lop3<LUT_BORROW>(B2, kb[2], w);
+                        w = lop3<LUT_BORROW>(B3, kb[3], w);
+                        w = lop3<LUT_BORROW>(B4, kb[4], w);
                         cnt += __popc(w);
                         runs_word(w, carry[j], sink);
                     }
