@@ -260,7 +260,7 @@ int make_plan(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_
     // warp work units (line pass): runs of `chunk` bands, series largest
     // first; about eight units per warp so the tail stays short while each
     // unit's histogram flush is spread over many cells
-    const int64_t n_warps = (int64_t)c->sm_count * 2 * WARPS;  // resident warps of the line pass
+    const int64_t n_warps = (int64_t)c->sm_count * 3 * WARPS;  // resident warps of the line pass
     auto chunk_for = [&](int64_t bands) {
         return (int32_t)std::max<int64_t>(4, std::min<int64_t>(64, bands / (n_warps * 8)));
     };

@@ -23,20 +23,30 @@
 namespace rqa {
 
 
+// Lines of length 1..WSH are counted in the warp's shared histogram; lengths
+// WSH+1..LSH go straight to the series' global short histogram and longer
+// ones to the caller's full histogram (both rare).
+constexpr int WSH = 48;
+
 template <bool HIST>
 struct LineSink {
     uint32_t *hs;           // this lane's column of the warp's shared histogram, [length][lane]
     uint64_t *hist;         // this series' full histogram row for lane k, or null
-    uint32_t lmax;          // longest line over LSH (shorter ones: read from hs at flush)
+    uint64_t *gshort;       // this series' global short histogram row for lane k
+    uint32_t lmax;          // longest line over WSH (shorter ones: read from hs at flush)
     uint32_t c1, c2, c3;    // interior lines of length 1, 2, 3, counted by popcount
     bool real;              // lane < K (the other lanes write a dummy row)
     // one line of length len; len == 0 means none (slot 0 is a scratch slot)
     __device__ __forceinline__ void emit(uint32_t len)
     {
-        hs[(len <= (uint32_t)LSH ? len : 0u) * 32u] += 1u;  // own column: own bank
-        if (len > (uint32_t)LSH) {  // rare
-            if (HIST && real)
-                atomicAdd(reinterpret_cast<unsigned long long *>(hist + (len - 1)), 1ull);
+        hs[(len <= (uint32_t)WSH ? len : 0u) * 32u] += 1u;  // own column: own bank
+        if (len > (uint32_t)WSH) {  // rare
+            if (real) {
+                if (len <= (uint32_t)LSH)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(gshort + (len - 1)), 1ull);
+                else if (HIST)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(hist + (len - 1)), 1ull);
+            }
             lmax = max(lmax, len);
         }
     }
@@ -111,9 +121,9 @@ __device__ __forceinline__ void runs_word(uint32_t w, uint32_t &c, Sink &sink)
 constexpr int TMAX = 512;
 
 // Per-warp shared memory: the warp's own short-line histogram laid out
-// [length 0..LSH][lane] (each lane owns one bank; length 0 is a scratch slot,
+// [length 0..WSH][lane] (each lane owns one bank; length 0 is a scratch slot,
 // lanes >= K own scratch columns), thresholds and rank table.
-__host__ __device__ constexpr int warp_smem_words() { return (LSH + 1) * 32 + 32 + TMAX; }
+__host__ __device__ constexpr int warp_smem_words() { return (WSH + 1) * 32 + 32 + TMAX; }
 
 int lines_smem_bytes(int) { return WARPS * warp_smem_words() * 4; }
 
@@ -138,12 +148,12 @@ __device__ __forceinline__ void unit_of(const CellArgs &a, int64_t u, int &s, in
 // its own histogram in shared memory, flushed when it moves to another series
 // and at exit.  No CTA-wide barrier, so no warp waits for another.
 template <int D, int M, int TAU, bool HIST>
-__global__ void __launch_bounds__(THREADS, 2) k_lines(CellArgs a, LineBufs lb, int K)
+__global__ void __launch_bounds__(THREADS, 3) k_lines(CellArgs a, LineBufs lb, int K)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *hs = reinterpret_cast<uint32_t *>(smem) + warp * warp_smem_words();
-    uint32_t *epsb = hs + (LSH + 1) * 32;
+    uint32_t *epsb = hs + (WSH + 1) * 32;
     uint32_t *tab = epsb + 32;
     const bool klane = lane < K;
 
@@ -153,7 +163,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_lines(CellArgs a, LineBufs lb, i
 #pragma unroll
     for (int b = 0; b < 5; ++b) kb[b] = (((lane + 1) >> b) & 1) ? FULL : 0u;
 
-    for (int x = lane; x < (LSH + 1) * 32; x += 32) hs[x] = 0;
+    for (int x = lane; x < (WSH + 1) * 32; x += 32) hs[x] = 0;
     __syncwarp();
 
     int cur = -1;
@@ -163,6 +173,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_lines(CellArgs a, LineBufs lb, i
     LineSink<HIST> sink;
     sink.hs = hs + lane;
     sink.hist = nullptr;
+    sink.gshort = nullptr;
     sink.lmax = 0;
     sink.c1 = sink.c2 = sink.c3 = 0;
     sink.real = klane;
@@ -177,7 +188,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_lines(CellArgs a, LineBufs lb, i
         uint64_t *gs = lb.hshort + ((int64_t)cur * K + lane) * LSH;
         uint32_t lm = sink.lmax;
 #pragma unroll 1
-        for (int l = 1; l <= LSH; ++l) {  // row l: one bank per lane
+        for (int l = 1; l <= WSH; ++l) {  // row l: one bank per lane
             const uint32_t v = hs[l * 32 + lane];
             if (klane && v) {
                 atomicAdd(reinterpret_cast<unsigned long long *>(gs + (l - 1)), (unsigned long long)v);
@@ -257,6 +268,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_lines(CellArgs a, LineBufs lb, i
             }
             if (HIST && klane)
                 sink.hist = lb.hist + lb.hist_off[s] + (int64_t)lane * (sd.ne - 1);
+            sink.gshort = lb.hshort + ((int64_t)s * K + (klane ? lane : 0)) * LSH;
             __syncwarp();
         }
         if (bad) continue;
