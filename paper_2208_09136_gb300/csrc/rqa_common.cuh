@@ -108,7 +108,7 @@ enum Embed : int { E_GENERIC = 0, E_M1 = 1, E_M2 = 2, E_M3 = 3, E_M4 = 4,
 
 // Host: CTAs of `kern` (THREADS threads, `smem` dynamic bytes) resident per
 // SM, and the SM count of the current device; both cached per host thread.
-inline int resident_per_sm(const void *kern, int smem)
+inline int resident_per_sm(const void *kern, int smem, int threads = THREADS)
 {
     struct Entry { const void *k; int s, v; };
     static thread_local Entry cache[64];
@@ -116,7 +116,7 @@ inline int resident_per_sm(const void *kern, int smem)
     for (int i = 0; i < n; ++i)
         if (cache[i].k == kern && cache[i].s == smem) return cache[i].v;
     int v = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, THREADS, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, threads, smem) != cudaSuccess) {
         cudaGetLastError();
         v = 1;
     }
@@ -138,11 +138,15 @@ inline int sm_count_current()
 }
 
 // A persistent grid: at most the CTAs that can be resident at once.
-inline int persistent_cap(const void *kern, int smem, int grid)
+inline int persistent_cap(const void *kern, int smem, int grid, int threads = THREADS)
 {
-    const int cap = sm_count_current() * resident_per_sm(kern, smem);
+    const int cap = sm_count_current() * resident_per_sm(kern, smem, threads);
     return grid < cap ? grid : (cap > 0 ? cap : 1);
 }
+
+// Threads per CTA of a counting round: rounds whose shared histogram allows
+// only two CTAs per SM run twice as many warps per CTA.
+__host__ __device__ constexpr int count_threads(int round) { return (round == 1 || round == 2) ? 512 : THREADS; }
 
 // Fetch the next work item for this CTA (one atomic per CTA), -1 when done.
 __device__ __forceinline__ int next_item(unsigned int *queue, int n_items, int *sh_slot)

@@ -77,8 +77,9 @@ __device__ __forceinline__ int bin_of(uint32_t key, const int8_t *t1, const int8
 // and final rounds look each key up in their group tables (the final round's
 // rare hits go straight to the global bins, so it needs no shared histogram).
 template <int ROUND, int M, int TAU>
-__global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K)
+__global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelBufs sb, int K)
 {
+    constexpr int NT = count_threads(ROUND);
     constexpr bool FILTERED = ROUND != R_COARSE;
     constexpr bool GLOBAL_BINS = ROUND == R_FINAL;  // final-round keys are rare: count in HBM
     extern __shared__ __align__(16) unsigned char smem[];
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
     int8_t *t2 = t1 + NCOARSE;
     const int lane = threadIdx.x & 31;
 
-    for (int x = threadIdx.x; x < nbins_max; x += THREADS) h[x] = 0;
+    for (int x = threadIdx.x; x < nbins_max; x += NT) h[x] = 0;
 
     for (;;) {
         const int it = next_item(a.queue, a.n_items, &slot);
@@ -125,10 +126,10 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
             const int8_t *src = (ROUND == R_COARSE_SUB) ? sb.tab_sub
                               : (ROUND == R_MID) ? sb.tab_mid : sb.tab_fin1;
             src += (int64_t)item.s * NCOARSE;
-            for (int x = threadIdx.x; x < NCOARSE; x += THREADS) t1[x] = src[x];
+            for (int x = threadIdx.x; x < NCOARSE; x += NT) t1[x] = src[x];
             if (ROUND == R_FINAL) {
                 const int8_t *s2 = sb.tab_fin2 + (int64_t)item.s * KMAX * NFINE;
-                for (int x = threadIdx.x; x < K * NFINE; x += THREADS) t2[1 + x] = s2[x];
+                for (int x = threadIdx.x; x < K * NFINE; x += NT) t2[1 + x] = s2[x];
                 if (threadIdx.x == 0) t2[0] = -1;
             }
             __syncthreads();
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(THREADS) k_count(CellArgs a, SelBufs sb, int K
                       below_sh);
         }
         uint64_t *gh = sb.hist + (int64_t)item.s * sb.hstride + (ROUND >= R_MID ? NCOARSE : 0);
-        for (int x = threadIdx.x; x < (GLOBAL_BINS ? 0 : nb_used); x += THREADS) {
+        for (int x = threadIdx.x; x < (GLOBAL_BINS ? 0 : nb_used); x += NT) {
             const uint32_t v = h[x];
             if (v) {
                 atomicAdd(reinterpret_cast<unsigned long long *>(gh + x), (unsigned long long)v);
@@ -242,8 +243,8 @@ static cudaError_t launch_count_m(const CellArgs &a, const SelBufs &sb, int K, i
     }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    grid = persistent_cap(reinterpret_cast<const void *>(kern), smem, grid);
-    kern<<<grid, THREADS, smem, st>>>(a, sb, K);
+    grid = persistent_cap(reinterpret_cast<const void *>(kern), smem, grid, count_threads(ROUND));
+    kern<<<grid, count_threads(ROUND), smem, st>>>(a, sb, K);
     return cudaGetLastError();
 }
 
