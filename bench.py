@@ -306,6 +306,7 @@ def main():
             dist.barrier()
 
     ctx = make_ctx(sched, have_model)
+    tuned_band = rqa.rqa_autotune(ctx, batch, RR, 100)  # keeps --band when one was given
     rqa.rqa_set_timing(ctx, True)
     for _ in range(args.warmup):
         step(ctx)
@@ -316,6 +317,7 @@ def main():
 
     clocks = ClockSampler(dev)
     launches0 = rqa.rqa_kernel_launches(ctx)
+    replays0 = rqa.rqa_graph_replays(ctx)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     phase = np.zeros(6, dtype=np.float64)
@@ -332,6 +334,7 @@ def main():
     barrier()
     clk = clocks.stop()
     launches = rqa.rqa_kernel_launches(ctx) - launches0
+    replays = rqa.rqa_graph_replays(ctx) - replays0
     bstats = rqa.rqa_bracket_stats(ctx) if have_model else None
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     code = rqa.rqa_status(ctx)
@@ -439,11 +442,13 @@ def main():
             "config": {"workload": args.workload, "desc": workload_desc(args.workload),
                        "form": f"{form} + radix select" if not have_model else f"{form} + learned bracket",
                        "series": S, "cells_per_step": total_cells, "l2": "flushed between steps",
-                       "line_band": rqa.rqa_device_info(ctx)["band"],
+                       "line_band": tuned_band,
+                       "line_band_from": "--band" if args.band else "rqa_autotune",
                        "parallelism": f"replicas x{world} (series-independent)"},
             "series_per_s": series_per_s,
             "phase_ms": {n: round(float(v), 4) for n, v in zip(names, phase)},
             "gpu_launches": int(launches),
+            "graph_replays": int(replays),
             "bracket": None if bstats is None else {"hits": bstats[0], "misses": bstats[1],
                                                     "miss_rate": bstats[1] / max(1, sum(bstats))},
             "roofline": roofline,

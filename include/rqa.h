@@ -89,8 +89,15 @@ typedef struct {
                           (1, any), (3, 1), (3, 3); otherwise 4 is used) */
     int blocks_per_sm; /* persistent CTAs per SM: 0 = as many as each kernel
                           can keep resident, else at most this many */
-    int reserved[4];   /* must be zero */
+    int flags;         /* RQA_FLAG_* */
+    int reserved[3];   /* must be zero */
 } rqa_config;
+
+/* rqa_det_avg records its launch sequence in a CUDA graph and replays it when
+ * the next call has the same arguments (batch layout and contents pointers,
+ * targets, outputs) -- only on a caller-owned stream, not on the legacy
+ * default stream.  This flag turns that off. */
+#define RQA_FLAG_NO_GRAPHS 1
 
 /* A batch of S series stored back to back in one device buffer. */
 typedef struct {
@@ -133,8 +140,19 @@ int rqa_device_info(rqa_ctx *ctx, int *sm_count, int *band, int *blocks_per_sm);
 int rqa_set_timing(rqa_ctx *ctx, int enable);
 int rqa_phase_times(rqa_ctx *ctx, float *ms, int n);
 
-/* Number of kernels this context has launched since it was created. */
+/* Number of kernels this context has launched since it was created (graph
+ * replays count the kernels of the graph). */
 uint64_t rqa_kernel_launches(rqa_ctx *ctx);
+
+/* Graph replays of rqa_det_avg since the context was created. */
+uint64_t rqa_graph_replays(rqa_ctx *ctx);
+
+/* Line-pass band width tuning: times the line pass over (a prefix of) the
+ * batch for each supported band width with the thresholds of rr_num/rr_den,
+ * keeps the fastest in the context (used while cfg.band was 0) and returns
+ * it in *band (host pointer, may be NULL).  Synchronises the stream. */
+int rqa_autotune(rqa_ctx *ctx, const rqa_batch *batch, const int32_t *rr_num, int32_t rr_den,
+                 int32_t K, int *band);
 
 /* ---- host helpers (no GPU needed) -------------------------------------- */
 

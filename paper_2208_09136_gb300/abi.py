@@ -40,7 +40,10 @@ class RqaError(RuntimeError):
 
 class _Config(ctypes.Structure):
     _fields_ = [("device", c_int), ("stream", c_vp), ("schedule", c_int), ("select", c_int),
-                ("band", c_int), ("blocks_per_sm", c_int), ("reserved", c_int * 4)]
+                ("band", c_int), ("blocks_per_sm", c_int), ("flags", c_int), ("reserved", c_int * 3)]
+
+
+RQA_FLAG_NO_GRAPHS = 1
 
 
 class _Batch(ctypes.Structure):
@@ -68,6 +71,8 @@ _SIGS = {
     "rqa_set_timing": ([c_vp, c_int], c_int),
     "rqa_phase_times": ([c_vp, c_vp, c_int], c_int),
     "rqa_kernel_launches": ([c_vp], c_u64),
+    "rqa_graph_replays": ([c_vp], c_u64),
+    "rqa_autotune": ([c_vp, ctypes.POINTER(_Batch), c_vp, c_i32, c_i32, c_vp], c_int),
     "rqa_line_hist": ([c_vp, ctypes.POINTER(_Batch), c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp],
                       c_int),
     "rqa_sketch": ([c_vp, ctypes.POINTER(_Batch), c_u64, c_vp, c_vp, c_vp], c_int),
@@ -186,13 +191,15 @@ class Context:
     """An ``rqa_ctx``: device, stream, schedule and scratch memory."""
 
     def __init__(self, device: int = 0, stream=None, schedule: int = RQA_SCHED_BATCHED,
-                 select: int = RQA_SELECT_AUTO, band: int = 0, blocks_per_sm: int = 0):
+                 select: int = RQA_SELECT_AUTO, band: int = 0, blocks_per_sm: int = 0,
+                 flags: int = 0):
         import torch
         if stream is None:
             stream = torch.cuda.current_stream(device)
         self.stream = stream
         handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-        cfg = _Config(device, c_vp(handle), schedule, select, band, blocks_per_sm, (c_int * 4)())
+        cfg = _Config(device, c_vp(handle), schedule, select, band, blocks_per_sm, int(flags),
+                      (c_int * 3)())
         p = c_vp()
         _check(lib().rqa_create(ctypes.byref(p), ctypes.byref(cfg)), "rqa_create")
         self._p = p
@@ -289,6 +296,20 @@ def rqa_phase_times(ctx: Context) -> np.ndarray:
 
 def rqa_kernel_launches(ctx: Context) -> int:
     return int(lib().rqa_kernel_launches(ctx.handle))
+
+
+def rqa_graph_replays(ctx: Context) -> int:
+    return int(lib().rqa_graph_replays(ctx.handle))
+
+
+def rqa_autotune(ctx: Context, batch: Batch, rr_num, rr_den: int) -> int:
+    """Pick the fastest line-pass band width for this batch; returns it."""
+    rr = np.ascontiguousarray(rr_num, dtype=np.int32)
+    b = batch._c()
+    band = c_int()
+    _check(lib().rqa_autotune(ctx.handle, ctypes.byref(b), _np_ptr(rr), int(rr_den), len(rr),
+                              ctypes.byref(band)), "rqa_autotune")
+    return band.value
 
 
 def rqa_line_hist(ctx: Context, batch: Batch, eps, K: int, hist=None, hist_offsets=None,

@@ -1,6 +1,7 @@
 // Host side of librqa: argument validation, work planning and the launch
 // sequences behind the C ABI declared in include/rqa.h.
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -21,10 +22,13 @@ struct DevBuf {
     size_t cap = 0;
 };
 
+std::atomic<uint64_t> g_realloc_events{0};  // any scratch reallocation (graphs capture pointers)
+
 int ensure(DevBuf &b, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
     if (bytes <= b.cap) return RQA_OK;
+    ++g_realloc_events;
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.cap = 0;
@@ -50,6 +54,7 @@ struct rqa_ctx {
     int select = RQA_SELECT_AUTO;
     int band = 16;          // diagonals per band of the counting rounds
     int band_lines = 0;     // ... of the line pass (0 = tuned default)
+    bool band_fixed = false;  // the caller chose the band: rqa_autotune keeps it
     int bpsm = 0;
     int sm_count = 0;
 
@@ -66,6 +71,15 @@ struct rqa_ctx {
     float margin = 0.f;
     DevBuf feats, centre, ymlp, acts, bstats, learn_scratch;
     uint64_t sketch_seed = 1;
+
+    // graph of the last rqa_det_avg call and its argument signature
+    bool graphs = true;
+    bool graph_valid = false;
+    std::vector<uint64_t> graph_sig;
+    cudaGraphExec_t graph_exec = nullptr;
+    uint64_t graph_launches = 0;  // kernels in the graph
+    uint64_t graph_replays = 0;
+    uint64_t alloc_gen = 0;       // bumped whenever a scratch buffer moves
 
     // per-phase timing of the last call (batched schedule)
     bool timing = false;
@@ -128,7 +142,9 @@ int launched(rqa_ctx *c, cudaError_t e)
 void mark(rqa_ctx *c, int i)
 {
     if (c->timing && c->schedule == RQA_SCHED_BATCHED) {
-        cudaEventRecord(c->ev[i], c->stream);
+        // "external": inside a stream capture this becomes an event-record node
+        // of the graph, so replays record the phase boundaries too
+        cudaEventRecordWithFlags(c->ev[i], c->stream, cudaEventRecordExternal);
         if (i == 6) c->ev_recorded = true;
     }
 }
@@ -319,6 +335,7 @@ int upload_plan(rqa_ctx *c, Plan &pl, const int32_t *lmin, int n_lmin, const int
         c->h_cap = total;
     }
     if (int rc = ensure(c->arena, total)) return rc;
+    c->graph_valid = false;  // the arena is about to hold another plan
     char *h = static_cast<char *>(c->h_stage);
     std::memcpy(h + o_sd, pl.sd.data(), pl.sd.size() * sizeof(SeriesDev));
     if (!pl.T.empty()) std::memcpy(h + o_T, pl.T.data(), pl.T.size() * sizeof(uint64_t));
@@ -670,8 +687,9 @@ int rqa_create(rqa_ctx **out, const rqa_config *cfg)
     rqa_config def;
     std::memset(&def, 0, sizeof(def));
     if (!cfg) cfg = &def;
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 3; ++i)
         if (cfg->reserved[i]) return RQA_ERR_INVALID_ARG;
+    if (cfg->flags & ~RQA_FLAG_NO_GRAPHS) return RQA_ERR_INVALID_ARG;
     if (cfg->schedule != RQA_SCHED_BATCHED && cfg->schedule != RQA_SCHED_PER_SERIES)
         return RQA_ERR_INVALID_ARG;
     if (cfg->select < RQA_SELECT_AUTO || cfg->select > RQA_SELECT_BRACKET) return RQA_ERR_INVALID_ARG;
@@ -692,6 +710,8 @@ int rqa_create(rqa_ctx **out, const rqa_config *cfg)
     c->select = cfg->select;
     c->band = BAND;
     c->band_lines = cfg->band;
+    c->band_fixed = cfg->band != 0;
+    c->graphs = !(cfg->flags & RQA_FLAG_NO_GRAPHS);
     c->bpsm = cfg->blocks_per_sm;
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess ||
@@ -728,6 +748,7 @@ void rqa_destroy(rqa_ctx *c)
     if (c->stage_done) cudaEventDestroy(c->stage_done);
     for (int i = 0; i < 7; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     cudaGetLastError();
     delete c;
 }
@@ -788,35 +809,101 @@ int rqa_det_avg(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t r
     cudaSetDevice(c->device);
     Plan pl;
     if (int rc = make_plan(c, b, eps ? nullptr : rr_num, rr_den, K, pl)) return rc;
+    // every scratch buffer sized before anything is enqueued (and captured)
     if (int rc = ensure_line_bufs(c, pl.S, K)) return rc;
     if (!eps)
         if (int rc = ensure_select_bufs(c, pl.S, K)) return rc;
+    if (bracket)
+        if (int rc = ensure_bracket_bufs(c, pl.S)) return rc;
+    if (int rc = ensure(c->queue, (size_t)(5 * pl.S + 8) * 64)) return rc;
     const int64_t *hoff = (lo && lo->hist) ? lo->hist_offsets : nullptr;
-    if (int rc = upload_plan(c, pl, lmin, n_lmin, hoff)) return rc;
-    const float *e = eps;
-    if (!eps) {
-        if (int rc = select_all(c, b, pl, P<float>(c->eps_tmp), P<uint64_t>(c->le_tmp),
-                                P<uint64_t>(c->lt_tmp), bracket))
-            return rc;
-        e = P<float>(c->eps_tmp);
-    } else {
-        mark(c, 0);
-        if (int rc = launched(c, launch_check_finite(b->y, pl.total, P<int>(c->status), c->stream)))
-            return rc;
-        for (int i = 1; i <= 4; ++i) mark(c, i);
+
+    // the call's signature: every argument the launch sequence depends on
+    const bool use_graph = c->graphs && c->stream != nullptr;
+    std::vector<uint64_t> sig;
+    auto make_sig = [&]() {
+        sig.clear();
+        auto put = [&](uint64_t v) { sig.push_back(v); };
+        auto ptr = [&](const void *p) { put((uint64_t)(uintptr_t)p); };
+        put((uint64_t)pl.S); put((uint64_t)K); put((uint64_t)n_lmin); put((uint64_t)rr_den);
+        put(bracket); put((uint64_t)c->schedule); put((uint64_t)pl.band_lines); put(c->timing);
+        uint32_t mb;
+        std::memcpy(&mb, &c->margin, 4);
+        put(mb);
+        put(g_realloc_events.load());
+        ptr(b->y); ptr(eps); ptr(det_out); ptr(det_avg); ptr(eps_used);
+        ptr(lo ? lo->hist : nullptr); ptr(lo ? lo->lmax : nullptr);
+        ptr(lo ? lo->count : nullptr); ptr(lo ? lo->stencil : nullptr);
+        for (int s = 0; s <= pl.S; ++s) put((uint64_t)b->offsets[s]);
+        for (int s = 0; s < pl.S; ++s) put(((uint64_t)(uint32_t)b->m[s] << 32) | (uint32_t)b->tau[s]);
+        for (int k = 0; !eps && k < K; ++k) put((uint64_t)rr_num[k]);
+        for (int j = 0; j < n_lmin; ++j) put((uint64_t)lmin[j]);
+        for (int s = 0; hoff && s <= pl.S; ++s) put((uint64_t)hoff[s]);
+    };
+    if (use_graph) {
+        make_sig();
+        if (c->graph_valid && c->graph_exec && sig == c->graph_sig) {
+            if (int rc = check_cuda(cudaGraphLaunch(c->graph_exec, c->stream))) return rc;
+            c->launches += c->graph_launches;
+            c->graph_replays++;
+            return RQA_OK;
+        }
     }
-    LineBufs lb;
-    if (int rc = lines_and_outputs(c, pl, e, lo, lb)) return rc;
-    if (int rc = launched(c, launch_finalize_det(lb, pl.d_sd, pl.S, K, pl.d_lmin, n_lmin, det_out,
-                                                 det_avg, c->stream)))
-        return rc;
-    if (int rc = line_outputs_tail(c, pl, lo, lb)) return rc;
-    mark(c, 6);
-    if (eps_used)
-        if (int rc = check_cuda(cudaMemcpyAsync(eps_used, e, (size_t)pl.S * K * 4,
-                                                cudaMemcpyDeviceToDevice, c->stream)))
+    if (int rc = upload_plan(c, pl, lmin, n_lmin, hoff)) return rc;
+
+    auto body = [&]() -> int {
+        const float *e = eps;
+        if (!eps) {
+            if (int rc = select_all(c, b, pl, P<float>(c->eps_tmp), P<uint64_t>(c->le_tmp),
+                                    P<uint64_t>(c->lt_tmp), bracket))
+                return rc;
+            e = P<float>(c->eps_tmp);
+        } else {
+            mark(c, 0);
+            if (int rc = launched(c, launch_check_finite(b->y, pl.total, P<int>(c->status), c->stream)))
+                return rc;
+            for (int i = 1; i <= 4; ++i) mark(c, i);
+        }
+        LineBufs lb;
+        if (int rc = lines_and_outputs(c, pl, e, lo, lb)) return rc;
+        if (int rc = launched(c, launch_finalize_det(lb, pl.d_sd, pl.S, K, pl.d_lmin, n_lmin, det_out,
+                                                     det_avg, c->stream)))
             return rc;
-    return RQA_OK;
+        if (int rc = line_outputs_tail(c, pl, lo, lb)) return rc;
+        mark(c, 6);
+        if (eps_used)
+            if (int rc = check_cuda(cudaMemcpyAsync(eps_used, e, (size_t)pl.S * K * 4,
+                                                    cudaMemcpyDeviceToDevice, c->stream)))
+                return rc;
+        return RQA_OK;
+    };
+    if (!use_graph) return body();
+
+    // record the sequence once, then launch the recording (and replay it for
+    // identical calls); any failure falls back to launching directly
+    const uint64_t l0 = c->launches;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return body();
+    }
+    const int rc = body();
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(c->stream, &g);
+    cudaGraphExec_t ex = nullptr;
+    if (rc != RQA_OK || ec != cudaSuccess || !g || cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        c->launches = l0;
+        return body();
+    }
+    cudaGraphDestroy(g);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = ex;
+    c->graph_launches = c->launches - l0;
+    make_sig();  // after the upload, which may have moved the arena
+    c->graph_sig = sig;
+    c->graph_valid = true;
+    return check_cuda(cudaGraphLaunch(ex, c->stream));
 }
 
 int rqa_line_hist(rqa_ctx *c, const rqa_batch *b, const float *eps, int32_t K, uint64_t *hist,
@@ -869,6 +956,70 @@ int rqa_phase_times(rqa_ctx *c, float *ms, int n)
 }
 
 uint64_t rqa_kernel_launches(rqa_ctx *c) { return c ? c->launches : 0; }
+
+uint64_t rqa_graph_replays(rqa_ctx *c) { return c ? c->graph_replays : 0; }
+
+int rqa_autotune(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_den, int32_t K,
+                 int *band)
+{
+    if (!c) return RQA_ERR_INVALID_ARG;
+    if (int rc = validate_batch(b)) return rc;
+    if (int rc = validate_rr(rr_num, rr_den, K)) return rc;
+    if (c->band_fixed) {
+        if (band) *band = c->band_lines;
+        return RQA_OK;
+    }
+    cudaSetDevice(c->device);
+    // sample: the longest prefix of the batch under ~2e10 cells (at least one series)
+    rqa_batch sb = *b;
+    uint64_t cells = 0;
+    int j = 0;
+    for (; j < b->n_series; ++j) {
+        const int64_t ne = (b->offsets[j + 1] - b->offsets[j]) - (int64_t)(b->m[j] - 1) * b->tau[j];
+        const uint64_t pc = (uint64_t)ne * (uint64_t)(ne - 1) / 2;
+        if (j > 0 && cells + pc > (uint64_t)2e10) break;
+        cells += pc;
+    }
+    sb.n_series = j;
+    Plan probe;
+    if (int rc = make_plan(c, &sb, nullptr, 0, K, probe)) return rc;
+    if (int rc = ensure(c->eps_tmp, (size_t)sb.n_series * K * 4)) return rc;
+    float *eps = P<float>(c->eps_tmp);
+    const int saved_select = c->select;
+    c->select = RQA_SELECT_RADIX;  // thresholds only: the plain selection suffices
+    int rc = rqa_eps_for_rr(c, &sb, rr_num, rr_den, K, eps, nullptr, nullptr);
+    c->select = saved_select;
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return check_cuda(cudaGetLastError());
+    const int saved_band = c->band_lines;
+    int best = DL_DEFAULT;
+    float best_ms = 3.4e38f;
+    const int cand[3] = {4, 8, 16};
+    for (int ci = 0; ci < 3 && rc == RQA_OK; ++ci) {
+        if (!lines_band_ok(probe.mt, cand[ci])) continue;
+        c->band_lines = cand[ci];
+        float t_min = 3.4e38f;
+        for (int rep = 0; rep < 2 && rc == RQA_OK; ++rep) {
+            cudaEventRecord(e0, c->stream);
+            rc = rqa_line_hist(c, &sb, eps, K, nullptr, nullptr, nullptr, nullptr, nullptr);
+            cudaEventRecord(e1, c->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = check_cuda(cudaGetLastError());
+            float ms = 0.f;
+            if (rc == RQA_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) t_min = std::min(t_min, ms);
+        }
+        if (t_min < best_ms) {
+            best_ms = t_min;
+            best = cand[ci];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->band_lines = rc == RQA_OK ? best : saved_band;
+    if (band) *band = c->band_lines;
+    return rc;
+}
 
 // ---------------------------------------------------------- learned bracket
 int rqa_sketch(rqa_ctx *c, const rqa_batch *b, uint64_t seed, float *feats, float *centre,

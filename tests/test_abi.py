@@ -71,7 +71,7 @@ def test_create_without_gpu_fails_cleanly(built):
     import ctypes
     from paper_2208_09136_gb300 import abi
     p = ctypes.c_void_p()
-    cfg = abi._Config(0, None, 0, 0, 0, 0, (ctypes.c_int * 4)())
+    cfg = abi._Config(0, None, 0, 0, 0, 0, 0, (ctypes.c_int * 3)())
     rc = abi.lib().rqa_create(ctypes.byref(p), ctypes.byref(cfg))
     assert rc == 4 and not p.value  # RQA_ERR_CUDA, no context
 
