@@ -275,9 +275,13 @@ cudaError_t adam_step(float *p, const float *g, float *m, float *v, int64_t n, i
 }
 
 // ------------------------------------------------------------ bracket
-// Coarse buckets to split in the first counting round: per target the
-// buckets between the keys of exp(c + lo - margin) and exp(c + hi + margin);
-// if the union is larger than NSUB_MAX only each target's middle bucket.
+// Coarse buckets to split in the first counting round.  Per target the
+// interval runs from the bucket of exp(c + lo - margin) to that of
+// exp(c + hi + margin).  If all of them fit in NSUB_MAX buckets, every bucket
+// from the lowest to the highest end is split (and up to two below); else the
+// buckets nearest each target's middle bucket first, then the narrowest gaps
+// between split buckets.  Keys between the first and the last split bucket
+// are counted either way (unsplit buckets at coarse resolution).
 __global__ void k_bracket(const float *__restrict__ Yb, const float *__restrict__ centre,
                           float margin, int K, int8_t *tab_sub, int32_t *n_sub, uint32_t *range)
 {
@@ -305,18 +309,58 @@ __global__ void k_bracket(const float *__restrict__ Yb, const float *__restrict_
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        int total = 0;  // size of the union of the targets' bucket ranges
-        int prev_hi = -1;
+        int lo_all = NCOARSE, hi_all = -1;
         for (int k = 0; k < K; ++k) {
-            const int a = max((int)lo_b[k], prev_hi + 1);
-            if ((int)hi_b[k] >= a) total += hi_b[k] - a + 1;
-            prev_hi = max(prev_hi, (int)hi_b[k]);
+            lo_all = min(lo_all, (int)lo_b[k]);
+            hi_all = max(hi_all, (int)hi_b[k]);
         }
-        if (total <= NSUB_MAX) {
-            for (int k = 0; k < K; ++k)
-                for (int b = lo_b[k]; b <= hi_b[k]; ++b) tb[b] = 0;
+        const int span = hi_all - lo_all + 1;
+        if (span <= NSUB_MAX) {
+            // every bucket from the lowest to the highest interval end: a
+            // threshold between two targets' intervals is found too; up to
+            // two more buckets below (they hold few keys)
+            const int a = max(0, lo_all - min(2, NSUB_MAX - span));
+            for (int b = a; b <= hi_all; ++b) tb[b] = 0;
         } else {
-            for (int k = 0; k < K; ++k) tb[mid_b[k]] = 0;
+            // rings around each target's most likely bucket, inside its
+            // interval, all targets alike, until the split budget is spent
+            int used = 0;
+            for (int r = 0; used < NSUB_MAX; ++r) {
+                bool any = false;
+                for (int k = 0; k < K; ++k) {
+                    for (int side = -1; side <= 1; side += 2) {
+                        if (r == 0 && side > 0) continue;
+                        const int b = (int)mid_b[k] + side * r;
+                        if (b < (int)lo_b[k] || b > (int)hi_b[k]) continue;
+                        any = true;
+                        if (tb[b] != 0 && used < NSUB_MAX) {
+                            tb[b] = 0;
+                            ++used;
+                        }
+                    }
+                }
+                if (!any) break;
+            }
+            // the rest of the budget closes the narrowest gaps between them
+            int first = 0, last = NCOARSE - 1;
+            while (first < NCOARSE && tb[first] != 0) ++first;
+            while (last > first && tb[last] != 0) --last;
+            for (;;) {
+                int best_a = -1, best_n = NCOARSE;
+                for (int b = first; b <= last; ++b) {
+                    if (tb[b] == 0) continue;
+                    int e = b;
+                    while (tb[e] != 0) ++e;  // tb[last] is marked: ends inside
+                    if (e - b < best_n) {
+                        best_n = e - b;
+                        best_a = b;
+                    }
+                    b = e;
+                }
+                if (best_a < 0 || used + best_n > NSUB_MAX) break;
+                for (int b = best_a; b < best_a + best_n; ++b) tb[b] = 0;
+                used += best_n;
+            }
         }
         int g = 0;  // marked buckets numbered in ascending order
         int first = -1, last = -1;

@@ -34,12 +34,15 @@ struct LineSink {
     uint64_t *hist;         // this series' full histogram row for lane k, or null
     uint64_t *gshort;       // this series' global short histogram row for lane k
     uint32_t lmax;          // longest line over WSH (shorter ones: read from hs at flush)
+    uint32_t longmass;      // cells on lines over WSH (the rest: sum of l * hs[l] at flush)
     uint32_t c1, c2, c3;    // interior lines of length 1, 2, 3, counted by popcount
     bool real;              // lane < K (the other lanes write a dummy row)
     // one line of length len; len == 0 means none (slot 0 is a scratch slot)
     __device__ __forceinline__ void emit(uint32_t len)
     {
-        hs[(len <= (uint32_t)WSH ? len : 0u) * 32u] += 1u;  // own column: own bank
+        // own column, own bank: no conflicts; one shared atomic instead of a
+        // load-add-store chain
+        atomicAdd(&hs[(len <= (uint32_t)WSH ? len : 0u) * 32u], 1u);
         if (len > (uint32_t)WSH) {  // rare
             if (real) {
                 if (len <= (uint32_t)LSH)
@@ -48,6 +51,7 @@ struct LineSink {
                     atomicAdd(reinterpret_cast<unsigned long long *>(hist + (len - 1)), 1ull);
             }
             lmax = max(lmax, len);
+            longmass += len;
         }
     }
     // fold the popcount tallies into the histogram column
@@ -169,12 +173,12 @@ __global__ void __launch_bounds__(THREADS, 3) k_lines(CellArgs a, LineBufs lb, i
     int cur = -1;
     bool bad = false;
     SeriesDev sd{};
-    uint32_t cnt = 0;  // recurrent cells of the lane's threshold in this unit
     LineSink<HIST> sink;
     sink.hs = hs + lane;
     sink.hist = nullptr;
     sink.gshort = nullptr;
     sink.lmax = 0;
+    sink.longmass = 0;
     sink.c1 = sink.c2 = sink.c3 = 0;
     sink.real = klane;
     int tshift = 0, tbase = 0, tbm1 = 0, tnb = 0;
@@ -187,6 +191,9 @@ __global__ void __launch_bounds__(THREADS, 3) k_lines(CellArgs a, LineBufs lb, i
         __syncwarp();
         uint64_t *gs = lb.hshort + ((int64_t)cur * K + lane) * LSH;
         uint32_t lm = sink.lmax;
+        // C_k is the line mass: sum over l of l * P_k(l) (every recurrent cell
+        // lies on exactly one line of its diagonal)
+        uint32_t cnt = sink.longmass;
 #pragma unroll 1
         for (int l = 1; l <= WSH; ++l) {  // row l: one bank per lane
             const uint32_t v = hs[l * 32 + lane];
@@ -194,6 +201,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_lines(CellArgs a, LineBufs lb, i
                 atomicAdd(reinterpret_cast<unsigned long long *>(gs + (l - 1)), (unsigned long long)v);
                 hs[l * 32 + lane] = 0;
                 lm = max(lm, (uint32_t)l);
+                cnt += (uint32_t)l * v;
             }
         }
         sink.lmax = lm;
@@ -203,8 +211,8 @@ __global__ void __launch_bounds__(THREADS, 3) k_lines(CellArgs a, LineBufs lb, i
                                (unsigned long long)cnt);
             if (sink.lmax) atomicMax(lb.lmax + o, sink.lmax);
         }
-        cnt = 0;
         sink.lmax = 0;
+        sink.longmass = 0;
         sink.c1 = sink.c2 = sink.c3 = 0;
         __syncwarp();
     };
@@ -284,14 +292,17 @@ __global__ void __launch_bounds__(THREADS, 3) k_lines(CellArgs a, LineBufs lb, i
                 uint32_t carry[D];
 #pragma unroll
                 for (int j = 0; j < D; ++j) carry[j] = 0;
-                for (int i0 = 0; i0 < rows; i0 += 32) {
+                // 32 rows of the band; INTERIOR: every cell inside the triangle
+                auto row_block = [&](int i0, auto interior) {
+                    constexpr bool INTERIOR = decltype(interior)::value;
                     const int i = i0 + lane;
                     BandTile<M, TAU, D> tile;
-                    tile.load(ys, sd.n, i, d_lo, rows, sd.tau, sd.m);
+                    if (INTERIOR) tile.load_fast(ys, i, d_lo, sd.tau);
+                    else tile.load(ys, sd.n, i, d_lo, rows, sd.tau, sd.m);
 #pragma unroll
                     for (int j = 0; j < D; ++j) {
                         const int dl = d_lo + j;
-                        const bool valid = i < sd.ne - dl;
+                        const bool valid = INTERIOR || i < sd.ne - dl;
                         uint32_t r = 31;  // outside the diagonal: recurrent for no k
                         // register windows read no memory per cell, so cells
                         // outside the triangle are computed and discarded
@@ -327,10 +338,12 @@ __global__ void __launch_bounds__(THREADS, 3) k_lines(CellArgs a, LineBufs lb, i
                         w = lop3<LUT_BORROW>(B2, kb[2], w);
                         w = lop3<LUT_BORROW>(B3, kb[3], w);
                         w = lop3<LUT_BORROW>(B4, kb[4], w);
-                        cnt += __popc(w);
                         runs_word(w, carry[j], sink);
                     }
-                }
+                };
+                int i0 = 0;
+                for (; i0 + 32 <= rows - (D - 1); i0 += 32) row_block(i0, std::true_type{});
+                for (; i0 < rows; i0 += 32) row_block(i0, std::false_type{});
 #pragma unroll
                 for (int j = 0; j < D; ++j) sink.emit(carry[j]);  // lines reaching the diagonal's end
             }
