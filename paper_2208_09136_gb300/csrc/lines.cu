@@ -118,18 +118,25 @@ __device__ __forceinline__ void runs_word(uint32_t w, uint32_t &c, Sink &sink)
     }
 }
 
-// Rank table: keys bucketed by key >> shift, at most one distinct threshold
-// value per bucket; entry = rank of a key up to that value (bits 0-4), rank
-// of a key above it (bits 5-9), and the value's offset inside the bucket
-// (bits 10-31, so shift <= 22).
-constexpr int TMAX = 512;
+// Rank table: keys bucketed by key >> shift (1 <= shift <= 22), at most one
+// distinct threshold value per bucket; entry = rank of a key up to that value
+// (bits 0-4), rank of a key above it (bits 5-9), and the value's offset
+// inside the bucket in the top `shift` bits.  One 32x32 -> 64-bit multiply of
+// the key by 2^(32-shift) gives the bucket (high word) and the key's offset
+// aligned with the entry's (low word): the low word is above the entry
+// exactly when the key is above the bucket's threshold, whatever bits 0-9
+// hold.
+constexpr int TMAX = 384;
 
 // Per-warp shared memory: the warp's own short-line histogram laid out
 // [length 0..WSH][lane] (each lane owns one bank; length 0 is a scratch slot,
 // lanes >= K own scratch columns), thresholds and rank table.
 __host__ __device__ constexpr int warp_smem_words() { return (WSH + 1) * 32 + 32 + TMAX; }
 
-int lines_smem_bytes(int) { return WARPS * warp_smem_words() * 4; }
+// CTAs of 4 warps: seven fit per SM (registers and shared memory), 28 warps
+constexpr int LTHREADS = 128;
+constexpr int LWARPS = LTHREADS / 32;
+int lines_smem_bytes(int) { return LWARPS * warp_smem_words() * 4; }
 
 // Series s and bands [b_lo, b_hi) of work unit u: a unit is a.chunk
 // consecutive bands of one series; units run over the series in a.order
@@ -152,7 +159,7 @@ __device__ __forceinline__ void unit_of(const CellArgs &a, int64_t u, int &s, in
 // its own histogram in shared memory, flushed when it moves to another series
 // and at exit.  No CTA-wide barrier, so no warp waits for another.
 template <int D, int M, int TAU, bool HIST>
-__global__ void __launch_bounds__(THREADS, 3) k_lines(CellArgs a, LineBufs lb, int K)
+__global__ void __launch_bounds__(LTHREADS, 7) k_lines(CellArgs a, LineBufs lb, int K)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -182,7 +189,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_lines(CellArgs a, LineBufs lb, i
     sink.c1 = sink.c2 = sink.c3 = 0;
     sink.real = klane;
     int tshift = 0, tbase = 0, tbm1 = 0, tnb = 0;
-    uint32_t tmask = 0;
+    uint32_t tmul = 0;  // 2^(32 - tshift)
     bool use_tab = false;
 
     auto flush = [&]() {
@@ -251,8 +258,8 @@ __global__ void __launch_bounds__(THREADS, 3) k_lines(CellArgs a, LineBufs lb, i
             tbase = (int)(vmin >> tshift);
             tbm1 = tbase - 1;
             tnb = (int)(vmax >> tshift) - tbase + 1;
-            tmask = (1u << tshift) - 1u;
-            use_tab = !bad && tnb + 2 <= TMAX;
+            tmul = tshift > 0 ? 1u << (32 - tshift) : 0u;
+            use_tab = !bad && tshift > 0 && tnb + 2 <= TMAX;
             __syncwarp();
             if (use_tab) {
                 for (int q = lane; q < tnb + 2; q += 32) {
@@ -267,9 +274,9 @@ __global__ void __launch_bounds__(THREADS, 3) k_lines(CellArgs a, LineBufs lb, i
                             const uint32_t ek = epsb[k];
                             const int eb = (int)(ek >> tshift) - tbase;
                             if (eb < q - 1) ++rlo;
-                            else if (eb == q - 1) { ++cnt; off = ek & tmask; }
+                            else if (eb == q - 1) { ++cnt; off = ek * tmul; }
                         }
-                        e = rlo | ((rlo + cnt) << 5) | (off << 10);
+                        e = rlo | ((rlo + cnt) << 5) | off;
                     }
                     tab[q] = e;
                 }
@@ -311,9 +318,10 @@ __global__ void __launch_bounds__(THREADS, 3) k_lines(CellArgs a, LineBufs lb, i
                                 __float_as_uint(tile.dist(ys, j, i, dl, sd.tau, sd.m));
                             uint32_t rk;
                             if (TABLE) {
-                                const int q = min(max((int)(key >> tshift) - tbm1, 0), tnb + 1);
+                                const uint64_t pk = (uint64_t)key * tmul;
+                                const int q = min(max((int)(uint32_t)(pk >> 32) - tbm1, 0), tnb + 1);
                                 const uint32_t e = tab[q];
-                                rk = (((key & tmask) > (e >> 10)) ? (e >> 5) : e) & 31u;
+                                rk = ((uint32_t)pk > e) ? (e >> 5) : e;  // bits 0-4: the rank
                             } else {
                                 rk = 0;
                                 rk += (epsb[rk + 15] < key) ? 16u : 0u;
@@ -391,8 +399,9 @@ static cudaError_t launch_lines_h(const CellArgs &a, const LineBufs &lb, int K, 
     const int smem = lines_smem_bytes(K);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    grid = persistent_cap(reinterpret_cast<const void *>(kern), smem, grid);
-    kern<<<grid, THREADS, smem, st>>>(a, lb, K);
+    grid *= WARPS / LWARPS;  // the caller counts CTAs of WARPS warps
+    grid = persistent_cap(reinterpret_cast<const void *>(kern), smem, grid, LTHREADS);
+    kern<<<grid, LTHREADS, smem, st>>>(a, lb, K);
     return cudaGetLastError();
 }
 

@@ -48,24 +48,13 @@ int count_smem_bytes(int round, int K)
     }
 }
 
-template <int ROUND>
-__device__ __forceinline__ int bin_of(uint32_t key, const int8_t *t1, const int8_t *t2)
+// *p += 1 in shared memory when pred holds, as one predicated reduction (no
+// branch, so a warp whose lanes disagree does not split).
+__device__ __forceinline__ void red_shared_if(uint32_t *p, bool pred)
 {
-    if (ROUND == R_COARSE) return (int)(key >> COARSE_SHIFT);
-    if (ROUND == R_COARSE_SUB) {
-        int c = (int)(key >> COARSE_SHIFT);
-        int g = t1[c];
-        return g < 0 ? c : NCOARSE + g * NFINE + (int)((key >> 10) & (NFINE - 1));
-    }
-    if (ROUND == R_MID) {
-        int g = t1[key >> COARSE_SHIFT];
-        return g < 0 ? -1 : g * NFINE + (int)((key >> 10) & (NFINE - 1));
-    }
-    // t2[0] is a -1 sentinel: no branch on the first lookup
-    const int g1 = t1[key >> COARSE_SHIFT];
-    const int idx = g1 < 0 ? 0 : 1 + g1 * NFINE + (int)((key >> 10) & (NFINE - 1));
-    const int g = t2[idx];
-    return g < 0 ? -1 : g * NFINE + (int)(key & (NFINE - 1));
+    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\t@q red.shared.add.u32 [%0], 1;\n\t}"
+                 :: "r"(a), "r"((uint32_t)pred) : "memory");
 }
 
 // One persistent launch over the work items; each CTA histograms the keys of
@@ -152,15 +141,10 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
             const int rows = sd.ne - d_lo;
             int last = -1;
             uint32_t run = 0;
-            // one cell's key into the histogram; consecutive cells of a lane
-            // are neighbours in the matrix, so equal bins are aggregated
-            auto count_key = [&](uint32_t key) {
-                const int bin = bin_of<ROUND>(key, t1, t2);
-                if (bin < 0) return;
-                if (GLOBAL_BINS) {
-                    atomicAdd(gbins + bin, 1ull);
-                    return;
-                }
+            // plain coarse round: every key counts and neighbouring cells of
+            // a lane often share a coarse bin, so equal bins are aggregated
+            auto count_coarse = [&](uint32_t key) {
+                const int bin = (int)(key >> COARSE_SHIFT);
                 if (bin == last) {
                     ++run;
                 } else {
@@ -169,20 +153,35 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
                     run = 1;
                 }
             };
-            // the 16 cells of a lane in one row block; valid = inside the triangle
+            // the BAND cells of a lane in one row block; valid = inside the
+            // triangle.  The filtered rounds are branch-free: the bin is
+            // computed for every cell (keys of finite or NaN distances have
+            // bit 31 clear, so key >> 20 indexes the 2048-entry table) and a
+            // predicated reduction counts the cells that fall in one.
             auto row_block = [&](const BandTile<M, TAU, BAND> &tile, int i, bool interior) {
 #pragma unroll
                 for (int j = 0; j < BAND; ++j) {
                     const int dl = d_lo + j;
                     const bool valid = interior || i < sd.ne - dl;
                     const uint32_t key = __float_as_uint(tile.dist(ys, j, i, dl, sd.tau, sd.m));
-                    if (ROUND == R_COARSE_SUB) {  // a quarter of the keys are inside the bracket
-                        if (valid) {
-                            if (key < klo) ++below;
-                            else if (key - klo <= kspan) count_key(key);
-                        }
-                    } else if (valid) {
-                        count_key(key);
+                    const int c = (int)(key >> COARSE_SHIFT);
+                    const int fine = (int)((key >> 10) & (NFINE - 1));
+                    if (ROUND == R_COARSE) {
+                        if (valid) count_coarse(key);
+                    } else if (ROUND == R_COARSE_SUB) {
+                        below += (valid && key < klo) ? 1u : 0u;
+                        const int g = t1[c];
+                        const int bin = g < 0 ? c : NCOARSE + g * NFINE + fine;
+                        red_shared_if(&h[bin], valid && key - klo <= kspan);
+                    } else if (ROUND == R_MID) {
+                        const int g = t1[c];
+                        red_shared_if(&h[max(g, 0) * NFINE + fine], valid && g >= 0);
+                    } else {
+                        // t2[0] is a -1 sentinel: no branch on the first lookup
+                        const int g1 = t1[c];
+                        const int g = t2[g1 < 0 ? 0 : 1 + g1 * NFINE + fine];
+                        if (valid && g >= 0)  // rare: a key of a target's 21-bit prefix
+                            atomicAdd(gbins + g * NFINE + (int)(key & (NFINE - 1)), 1ull);
                     }
                 }
             };
