@@ -35,7 +35,8 @@ struct LineSink {
     uint64_t *gshort;       // this series' global short histogram row for lane k
     uint32_t lmax;          // longest line over WSH (shorter ones: read from hs at flush)
     uint32_t longmass;      // cells on lines over WSH (the rest: sum of l * hs[l] at flush)
-    uint32_t c1, c2, c3;    // interior lines of length 1, 2, 3, counted by popcount
+    uint32_t cp;            // interior lines of length 1, 2, 3 counted by popcount,
+                            // packed in 10-bit fields (bits 0, 10, 20)
     bool real;              // lane < K (the other lanes write a dummy row)
     // one line of length len; len == 0 means none (slot 0 is a scratch slot)
     __device__ __forceinline__ void emit(uint32_t len)
@@ -57,10 +58,10 @@ struct LineSink {
     // fold the popcount tallies into the histogram column
     __device__ __forceinline__ void settle()
     {
-        hs[1 * 32] += c1;
-        hs[2 * 32] += c2;
-        hs[3 * 32] += c3;
-        c1 = c2 = c3 = 0;
+        hs[1 * 32] += cp & 1023u;
+        hs[2 * 32] += (cp >> 10) & 1023u;
+        hs[3 * 32] += cp >> 20;
+        cp = 0;
     }
 };
 
@@ -108,9 +109,9 @@ __device__ __forceinline__ void runs_word(uint32_t w, uint32_t &c, Sink &sink)
     const uint32_t s3 = s2 & (mid >> 2);         // >= 3
     uint32_t x = s3 & (mid >> 3);                // >= 4
     const uint32_t n1 = __popc(st), n2 = __popc(s2), n3 = __popc(s3);
-    sink.c1 += n1 - n2;
-    sink.c2 += n2 - n3;
-    sink.c3 += n3 - __popc(x);
+    // (n1 - n2) + (n2 - n3) 2^10 + (n3 - n4) 2^20 as multiply-adds: each field
+    // grows by at most 15 per word (interior lines need a zero between them)
+    sink.cp += n1 + n2 * 1023u + n3 * 0xFFC00u - (uint32_t)__popc(x) * 0x100000u;
     while (x) {
         const int p = __ffs(x) - 1;
         sink.emit((uint32_t)(__ffs(~(mid >> p)) - 1));
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(LTHREADS, 7) k_lines(CellArgs a, LineBufs lb, 
     sink.gshort = nullptr;
     sink.lmax = 0;
     sink.longmass = 0;
-    sink.c1 = sink.c2 = sink.c3 = 0;
+    sink.cp = 0;
     sink.real = klane;
     int tshift = 0, tbase = 0, tbm1 = 0, tnb = 0;
     uint32_t tmul = 0;  // 2^(32 - tshift)
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(LTHREADS, 7) k_lines(CellArgs a, LineBufs lb, 
         }
         sink.lmax = 0;
         sink.longmass = 0;
-        sink.c1 = sink.c2 = sink.c3 = 0;
+        sink.cp = 0;
         __syncwarp();
     };
 
@@ -349,9 +350,25 @@ __global__ void __launch_bounds__(LTHREADS, 7) k_lines(CellArgs a, LineBufs lb, 
                         runs_word(w, carry[j], sink);
                     }
                 };
-                int i0 = 0;
-                for (; i0 + 32 <= rows - (D - 1); i0 += 32) row_block(i0, std::true_type{});
-                for (; i0 < rows; i0 += 32) row_block(i0, std::false_type{});
+                // the packed tallies take 1023 / (15 D) row blocks before a
+                // field could overflow
+                constexpr int SETTLE = 1023 / (15 * D);
+                int i0 = 0, nrb = 0;
+                for (; i0 + 32 <= rows - (D - 1); i0 += 32) {
+                    row_block(i0, std::true_type{});
+                    if (++nrb == SETTLE) {
+                        sink.settle();
+                        nrb = 0;
+                    }
+                }
+                for (; i0 < rows; i0 += 32) {
+                    row_block(i0, std::false_type{});
+                    if (++nrb == SETTLE) {
+                        sink.settle();
+                        nrb = 0;
+                    }
+                }
+                sink.settle();
 #pragma unroll
                 for (int j = 0; j < D; ++j) sink.emit(carry[j]);  // lines reaching the diagonal's end
             }
