@@ -60,7 +60,7 @@ struct rqa_ctx {
 
     // scratch (grow-only)
     DevBuf arena;      // uploaded plan: series, targets, items, lmin, hist offsets
-    DevBuf prefix, level, rank, below, tab_sub, tab_mid, tab_fin1, tab_fin2, ngroups, hist, krange,
+    DevBuf prefix, level, rank, below, tab_sub, tab_mid, tab_fin1, tab_fin2, tab_hash, ngroups, hist, krange,
         redo;
     DevBuf queue, status;
     DevBuf eps_tmp, le_tmp, lt_tmp, count, lmax, hshort;
@@ -378,6 +378,7 @@ int ensure_select_bufs(rqa_ctx *c, int S, int K)
     if ((rc = ensure(c->tab_mid, (size_t)S * NCOARSE))) return rc;
     if ((rc = ensure(c->tab_fin1, (size_t)S * NCOARSE))) return rc;
     if ((rc = ensure(c->tab_fin2, (size_t)S * KMAX * NFINE))) return rc;
+    if ((rc = ensure(c->tab_hash, (size_t)S * NHASH * 4))) return rc;
     if ((rc = ensure(c->ngroups, (size_t)S * 4 * sizeof(int32_t)))) return rc;
     if ((rc = ensure(c->krange, (size_t)S * 2 * sizeof(uint32_t)))) return rc;
     if ((rc = ensure(c->redo, (size_t)S))) return rc;
@@ -390,7 +391,7 @@ int ensure_select_bufs(rqa_ctx *c, int S, int K)
 
 SelBufs sel_bufs(rqa_ctx *c, const Plan &pl)
 {
-    SelBufs sb;
+    SelBufs sb{};
     sb.T = pl.d_T;
     sb.prefix = P<uint32_t>(c->prefix);
     sb.level = P<uint8_t>(c->level);
@@ -404,6 +405,8 @@ SelBufs sel_bufs(rqa_ctx *c, const Plan &pl)
     sb.n_sub = ng;
     sb.n_mid = ng + pl.S;
     sb.n_fin = ng + 2 * pl.S;
+    sb.tab_hash = P<uint32_t>(c->tab_hash);
+    sb.hash_mul = reinterpret_cast<uint32_t *>(ng + 3 * pl.S);
     sb.hist = P<uint64_t>(c->hist);
     sb.hstride = hist_stride(pl.K);
     sb.range = P<uint32_t>(c->krange);
@@ -736,7 +739,8 @@ void rqa_destroy(rqa_ctx *c)
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->arena, &c->prefix, &c->level, &c->rank, &c->below, &c->tab_sub,
-                      &c->tab_mid, &c->tab_fin1, &c->tab_fin2, &c->ngroups, &c->hist, &c->krange,
+                      &c->tab_mid, &c->tab_fin1, &c->tab_fin2, &c->tab_hash, &c->ngroups, &c->hist,
+                      &c->krange,
                       &c->redo,
                       &c->queue,
                       &c->status, &c->eps_tmp, &c->le_tmp, &c->lt_tmp, &c->count, &c->lmax,

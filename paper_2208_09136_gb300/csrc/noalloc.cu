@@ -199,7 +199,7 @@ extern "C" int rqa_eps_for_rr_noalloc(const rqa_batch *b, const int32_t *rr_num,
     int *status = reinterpret_cast<int *>(scr + O_STATUS);
     if (launch_check_finite(b->y, b->offsets[pl.S], status, st) != cudaSuccess) return RQA_ERR_CUDA;
 
-    SelBufs sb;
+    SelBufs sb{};  // no hashed final-round table here: tab_hash = hash_mul = null
     sb.T = reinterpret_cast<const uint64_t *>(scr + O_T);
     sb.prefix = reinterpret_cast<uint32_t *>(scr + O_PREFIX);
     sb.level = reinterpret_cast<uint8_t *>(scr + O_LEVEL);

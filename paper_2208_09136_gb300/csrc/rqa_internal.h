@@ -13,6 +13,8 @@ constexpr int KMAX = 31;
 constexpr int COARSE_SHIFT = 20;
 constexpr int NCOARSE = 1 << 11;   // 2048 coarse buckets
 constexpr int NFINE = 1 << 10;     // 1024 bins per middle / low digit group
+constexpr int NHASH_BITS = 12;     // final round: hashed table of the targets' 21-bit prefixes
+constexpr int NHASH = 1 << NHASH_BITS;
 constexpr int NSUB_MAX = 24;       // bracket-subdivided coarse buckets per series
 constexpr int LSH = 64;            // line lengths 1..LSH counted in shared memory
 constexpr int LMIN_MAX = 8;        // entries of an lmin list
@@ -54,6 +56,9 @@ struct SelBufs {
     int8_t *tab_mid;       // [s][NCOARSE] coarse bucket -> middle group, -1
     int8_t *tab_fin1;      // [s][NCOARSE] coarse bucket -> final super group, -1
     int8_t *tab_fin2;      // [s][KMAX][NFINE] (super group, middle digit) -> group
+    uint32_t *tab_hash;    // [s][NHASH] prefix | group << 21 at slot (prefix * mul) >> 20,
+                           // 0xffffffff empty; may be null (two-level tables only)
+    uint32_t *hash_mul;    // [s]: the slot multiplier, 0 = no collision-free one (or no table)
     int32_t *n_sub, *n_mid, *n_fin;   // [s]
     uint32_t *range;       // [s][2]: keys the next filtered round can count, inclusive
     uint8_t *redo;         // [s]: 1 = the plain coarse round runs for this series

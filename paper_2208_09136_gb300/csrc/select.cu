@@ -14,6 +14,7 @@
 // below) per target.  After R_FINAL the key is complete: eps_k, and
 // #{d < eps_k} = below, #{d <= eps_k} = below + (keys equal to eps_k).
 #include <cstdint>
+#include <type_traits>
 #include "rqa_common.cuh"
 
 namespace rqa {
@@ -44,7 +45,10 @@ int count_smem_bytes(int round, int K)
     case R_COARSE: return NCOARSE * 4;
     case R_COARSE_SUB: return (NCOARSE + NSUB_MAX * NFINE) * 4 + NCOARSE;
     case R_MID: return K * NFINE * 4 + NCOARSE;
-    default: return NCOARSE + 1 + K * NFINE;  // tables only: final-round keys are rare
+    default: {  // tables only (final-round keys are rare): the hash or the two levels
+        const int two = NCOARSE + 1 + K * NFINE;
+        return two > NHASH * 4 ? two : NHASH * 4;
+    }
     }
 }
 
@@ -74,6 +78,7 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int slot;
     __shared__ int nb_used_sh;
+    __shared__ uint32_t hmul_sh;
     __shared__ int next_band;
     __shared__ uint32_t key_lo, key_hi;
     __shared__ unsigned long long below_sh;
@@ -83,6 +88,7 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
     uint32_t *h = reinterpret_cast<uint32_t *>(smem);
     int8_t *t1 = reinterpret_cast<int8_t *>(h + nbins_max);
     int8_t *t2 = t1 + NCOARSE;
+    uint32_t *th = reinterpret_cast<uint32_t *>(smem);  // final round, hashed: instead of t1/t2
     const int lane = threadIdx.x & 31;
 
     for (int x = threadIdx.x; x < nbins_max; x += NT) h[x] = 0;
@@ -107,11 +113,17 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
                 key_hi = sb.range[2 * (int64_t)item.s + 1];
             }
             below_sh = 0ull;
+            hmul_sh = (ROUND == R_FINAL && sb.hash_mul) ? sb.hash_mul[item.s] : 0u;
         }
         __syncthreads();
         const int nb_used = nb_used_sh;
+        const uint32_t hmul = hmul_sh;
         if (nb_used == 0) continue;  // no target of this series needs this round
-        if (ROUND != R_COARSE) {
+        if (ROUND == R_FINAL && hmul) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(sb.tab_hash + (int64_t)item.s * NHASH);
+            for (int x = threadIdx.x; x < NHASH / 4; x += NT) reinterpret_cast<uint4 *>(th)[x] = src[x];
+            __syncthreads();
+        } else if (ROUND != R_COARSE) {
             const int8_t *src = (ROUND == R_COARSE_SUB) ? sb.tab_sub
                               : (ROUND == R_MID) ? sb.tab_mid : sb.tab_fin1;
             src += (int64_t)item.s * NCOARSE;
@@ -129,6 +141,10 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
         unsigned long long *gbins =
             reinterpret_cast<unsigned long long *>(sb.hist + (int64_t)item.s * sb.hstride + NCOARSE);
         uint32_t below = 0;  // bracket round: keys under its range
+        const uint32_t nfin = (uint32_t)(nb_used / NFINE);
+        // the item's bands; HASHED: final round with the hashed prefix table
+        auto item_bands = [&](auto hashed) {
+        constexpr bool HASHED = decltype(hashed)::value;
         for (;;) {
             // bands are handed to warps one at a time, so no warp idles while
             // another still has several bands of the item left
@@ -176,6 +192,15 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
                     } else if (ROUND == R_MID) {
                         const int g = t1[c];
                         red_shared_if(&h[max(g, 0) * NFINE + fine], valid && g >= 0);
+                    } else if (HASHED) {
+                        // one probe: the slot holds the only target prefix
+                        // that can map there (group < nfin guards the empty
+                        // slots and any NaN key)
+                        const uint32_t pfx = key >> 10;
+                        const uint32_t e = th[(pfx * hmul) >> (32 - NHASH_BITS)];
+                        const uint32_t g = e >> 21;
+                        if (valid && ((e ^ pfx) & 0x1FFFFFu) == 0u && g < nfin)  // rare
+                            atomicAdd(gbins + g * NFINE + (key & (NFINE - 1)), 1ull);
                     } else {
                         // t2[0] is a -1 sentinel: no branch on the first lookup
                         const int g1 = t1[c];
@@ -199,6 +224,9 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
             }
             if (run) atomicAdd(&h[last], run);
         }
+        };
+        if (ROUND == R_FINAL && hmul) item_bands(std::true_type{});
+        else item_bands(std::false_type{});
         if (ROUND == R_COARSE_SUB) {
             // keys under the bracket: one count, kept in the coarse bucket
             // just below it (every bucket under it is empty in this round)
@@ -478,8 +506,10 @@ k_select(SelBufs sb, const SeriesDev *series, int s_begin, int K, float *eps_out
         // final-round tables for all targets (every target is at level 2 now)
         int8_t *f1 = sb.tab_fin1 + (int64_t)s * NCOARSE;
         int8_t *f2 = sb.tab_fin2 + (int64_t)s * KMAX * NFINE;
+        uint32_t *fh = sb.tab_hash ? sb.tab_hash + (int64_t)s * NHASH : nullptr;
         for (int x = t; x < NCOARSE; x += THREADS) f1[x] = -1;
         for (int x = t; x < K * NFINE; x += THREADS) f2[x] = -1;
+        for (int x = t; fh && x < NHASH; x += THREADS) fh[x] = 0xffffffffu;
         __syncthreads();
         if (t == 0) {
             int g1 = 0, g = 0;
@@ -495,6 +525,28 @@ k_select(SelBufs sb, const SeriesDev *series, int s_begin, int K, float *eps_out
             sb.n_fin[s] = g;
             sb.range[2 * (int64_t)s] = lo;
             sb.range[2 * (int64_t)s + 1] = hi;
+            // hashed table of the distinct prefixes (group order): the first
+            // odd multiplier of a fixed sequence that puts them in distinct
+            // slots; none among 64 (never seen) keeps the two-level tables
+            if (fh) {
+                uint32_t pg[KMAX];
+                for (int k = 0; k < K; ++k) {
+                    const int gk = f2[f1[pre[k] >> 10] * NFINE + (pre[k] & (NFINE - 1))];
+                    pg[gk] = pre[k];
+                }
+                uint32_t mul = 0;
+                for (int a = 0; a < 64 && !mul; ++a) {
+                    const uint32_t m = (0x9E3779B1u + 0x6A09E668u * (uint32_t)a) | 1u;
+                    bool ok = true;
+                    for (int i = 1; i < g && ok; ++i)
+                        for (int j = 0; j < i && ok; ++j)
+                            ok = ((pg[i] * m) >> (32 - NHASH_BITS)) != ((pg[j] * m) >> (32 - NHASH_BITS));
+                    if (ok) mul = m;
+                }
+                if (mul)
+                    for (int i = 0; i < g; ++i) fh[(pg[i] * mul) >> (32 - NHASH_BITS)] = pg[i] | ((uint32_t)i << 21);
+                sb.hash_mul[s] = mul;
+            }
         }
         if (t < K) {
             sb.prefix[sk + t] = pre[t];
