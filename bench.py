@@ -147,13 +147,13 @@ def file_hash(path):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
 
-def profile_traffic(kernel_key):
-    """DRAM bytes per launch of a kernel from a committed ncu summary, if the
-    kernel source has not changed since it was captured."""
+def profile_traffic(kernel_key, workload):
+    """DRAM bytes per launch of a kernel from a committed ncu summary, if it was
+    taken on this workload and the kernel source has not changed since."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel_key]
         src = os.path.join(ROOT, rec["source"])
-        if file_hash(src) != rec["source_sha"]:
+        if file_hash(src) != rec["source_sha"] or rec.get("workload") != workload:
             return None
         return rec
     except Exception:
@@ -416,11 +416,16 @@ def main():
     ops_cell = {4: (2 * mm - 1) + 5 + 0.2, 1: (2 * mm - 1) + 2, 2: (2 * mm - 1) + 2,
                 3: (2 * mm - 1) + 2}.get(dom, 0.0)
     achieved = total_cells * ops_cell / (phase[dom] * 1e-3) if phase[dom] > 0 else 0.0
-    traffic = profile_traffic("lines" if dom == 4 else "count")
+    traffic = profile_traffic("lines" if dom == 4 else "count", args.workload)
     roofline = {"bound": "alu", "kernel": names[dom], "achieved": achieved / 1e12,
                 "peak": peak_ops / 1e12, "unit": "Tops/s (lane-ops)",
                 "frac": achieved / peak_ops if peak_ops else None,
                 "traffic": None if traffic is None else traffic["bytes_per_launch"],
+                "ncu": None if traffic is None or "issue_active_pct" not in traffic else {
+                    "issue_active_pct": traffic["issue_active_pct"],
+                    "alu_pipe_pct": traffic["alu_pipe_pct"],
+                    "warp_inst_per_32_cells": round(traffic["warp_instructions"] * 32 / total_cells, 1),
+                    "source": "profiles/traffic.json (one ncu pass of the same kernel on this workload)"},
                 "ops_per_cell": ops_cell,
                 "peak_note": f"{sm} SMs x 128 lanes x {f_max/1e6:.0f} MHz (max SM clock)"}
 

@@ -29,7 +29,12 @@ def full_run(rqa_lib):
     out = rqa.det_avg(ctx, batch, RR20, 100, lmin=LMIN, lines=True)
     assert rqa.rqa_status(ctx) == 0
     hits, misses = rqa.rqa_bracket_stats(ctx)
+    sel = rqa.eps_for_rr(ctx, batch, RR20, 100)  # the selection alone, for its own counts
+    assert rqa.rqa_status(ctx) == 0
     res = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in out.items()}
+    res["sel_eps"] = sel["eps"].cpu().numpy()
+    res["sel_le"] = sel["count_le"].cpu().numpy()
+    res["sel_lt"] = sel["count_lt"].cpu().numpy()
     res["hist_list"] = rqa.unpack_hist(res["hist"], res["hist_offsets"], batch, 20)
     ctx.close()
     return w, flat, offsets, m, tau, res, (hits, misses)
@@ -39,6 +44,20 @@ def test_bracket_statistics(full_run):
     _, _, offsets, _, _, res, (hits, misses) = full_run
     assert hits + misses == (len(offsets) - 1) * 20
     assert misses / (hits + misses) < 0.05
+
+
+def test_line_mass_equals_selection_count(full_run):
+    """C_k from the line pass (sum of l P_k(l)) against the selection's own
+    #{d <= eps_k}, and the counting certificate #{d < eps_k} < T_k <= C_k,
+    on every series: two independent counts of the same recurrent cells."""
+    _, _, offsets, m, tau, res, _ = full_run
+    assert np.array_equal(res["sel_eps"], res["eps"])
+    assert np.array_equal(res["sel_le"], res["count"])
+    for s in range(len(offsets) - 1):
+        ne = int(offsets[s + 1] - offsets[s]) - (int(m[s]) - 1) * int(tau[s])
+        P = ne * (ne - 1) // 2
+        T = np.array([-((-r * P) // 100) for r in RR20], dtype=np.uint64)
+        assert np.all(res["sel_lt"][s] < T) and np.all(T <= res["sel_le"][s]), s
 
 
 def test_invariants_every_series(full_run):
