@@ -52,13 +52,17 @@ int count_smem_bytes(int round, int K)
     }
 }
 
-// *p += 1 in shared memory when pred holds, as one predicated reduction (no
-// branch, so a warp whose lanes disagree does not split).
-__device__ __forceinline__ void red_shared_if(uint32_t *p, bool pred)
+// Add 1 to the shared word at shared-space address a when pred holds, as
+// one predicated reduction (no branch, so a warp whose lanes disagree does
+// not split; a is not touched when pred is false).
+__device__ __forceinline__ void red_shared_addr_if(uint32_t a, bool pred)
 {
-    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
     asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\t@q red.shared.add.u32 [%0], 1;\n\t}"
                  :: "r"(a), "r"((uint32_t)pred) : "memory");
+}
+__device__ __forceinline__ void red_shared_if(uint32_t *p, bool pred)
+{
+    red_shared_addr_if(static_cast<uint32_t>(__cvta_generic_to_shared(p)), pred);
 }
 
 // One persistent launch over the work items; each CTA histograms the keys of
@@ -142,9 +146,16 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
             reinterpret_cast<unsigned long long *>(sb.hist + (int64_t)item.s * sb.hstride + NCOARSE);
         uint32_t below = 0;  // bracket round: keys under its range
         const uint32_t nfin = (uint32_t)(nb_used / NFINE);
-        // the item's bands; HASHED: final round with the hashed prefix table
-        auto item_bands = [&](auto hashed) {
-        constexpr bool HASHED = decltype(hashed)::value;
+        // bracket round with every bucket from the first to the last split
+        // one split (the usual case): split group g is bucket first + g, so
+        // the bin is (key - klo) >> 10 past the coarse bins, no table
+        const bool dense = ROUND == R_COARSE_SUB && ((kspan >> COARSE_SHIFT) + 1u) * NFINE + NCOARSE ==
+                                                        (uint32_t)nb_used;
+        const uint32_t hsub = static_cast<uint32_t>(__cvta_generic_to_shared(h + NCOARSE));
+        // the item's bands; FAST: dense bracket round, or final round with the
+        // hashed prefix table
+        auto item_bands = [&](auto fast) {
+        constexpr bool FAST = decltype(fast)::value;
         for (;;) {
             // bands are handed to warps one at a time, so no warp idles while
             // another still has several bands of the item left
@@ -184,6 +195,11 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
                     const int fine = (int)((key >> 10) & (NFINE - 1));
                     if (ROUND == R_COARSE) {
                         if (valid) count_coarse(key);
+                    } else if (ROUND == R_COARSE_SUB && FAST) {
+                        // keys under klo wrap to rel >= 2^31 (keys are < 2^31)
+                        const uint32_t rel = key - klo;
+                        below += valid ? rel >> 31 : 0u;
+                        red_shared_addr_if(hsub + ((rel >> 10) << 2), valid && rel <= kspan);
                     } else if (ROUND == R_COARSE_SUB) {
                         below += (valid && key < klo) ? 1u : 0u;
                         const int g = t1[c];
@@ -192,7 +208,7 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
                     } else if (ROUND == R_MID) {
                         const int g = t1[c];
                         red_shared_if(&h[max(g, 0) * NFINE + fine], valid && g >= 0);
-                    } else if (HASHED) {
+                    } else if (FAST) {
                         // one probe: the slot holds the only target prefix
                         // that can map there (group < nfin guards the empty
                         // slots and any NaN key)
@@ -225,7 +241,7 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
             if (run) atomicAdd(&h[last], run);
         }
         };
-        if (ROUND == R_FINAL && hmul) item_bands(std::true_type{});
+        if ((ROUND == R_FINAL && hmul) || dense) item_bands(std::true_type{});
         else item_bands(std::false_type{});
         if (ROUND == R_COARSE_SUB) {
             // keys under the bracket: one count, kept in the coarse bucket
@@ -349,7 +365,6 @@ k_select(SelBufs sb, const SeriesDev *series, int s_begin, int K, float *eps_out
     __shared__ uint8_t lev[KMAX];
     __shared__ uint64_t rnk[KMAX], blw[KMAX];
     __shared__ int grp[KMAX];
-    __shared__ int ngroups;
     const int s = s_begin + blockIdx.x;
     const int t = threadIdx.x;
     const int64_t sk = (int64_t)s * K;
