@@ -57,7 +57,7 @@ struct SelBufs {
     int8_t *tab_fin1;      // [s][NCOARSE] coarse bucket -> final super group, -1
     int8_t *tab_fin2;      // [s][KMAX][NFINE] (super group, middle digit) -> group
     uint32_t *tab_hash;    // [s][NHASH] prefix | group << 21 at slot (prefix * mul) >> 20,
-                           // 0xffffffff empty; may be null (two-level tables only)
+                           // 0x1fffff empty; may be null (two-level tables only)
     uint32_t *hash_mul;    // [s]: the slot multiplier, 0 = no collision-free one (or no table)
     int32_t *n_sub, *n_mid, *n_fin;   // [s]
     uint32_t *range;       // [s][2]: keys the next filtered round can count, inclusive

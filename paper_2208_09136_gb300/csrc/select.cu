@@ -145,7 +145,6 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
         unsigned long long *gbins =
             reinterpret_cast<unsigned long long *>(sb.hist + (int64_t)item.s * sb.hstride + NCOARSE);
         uint32_t below = 0;  // bracket round: keys under its range
-        const uint32_t nfin = (uint32_t)(nb_used / NFINE);
         // bracket round with every bucket from the first to the last split
         // one split (the usual case): split group g is bucket first + g, so
         // the bin is (key - klo) >> 10 past the coarse bins, no table
@@ -210,13 +209,13 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
                         red_shared_if(&h[max(g, 0) * NFINE + fine], valid && g >= 0);
                     } else if (FAST) {
                         // one probe: the slot holds the only target prefix
-                        // that can map there (group < nfin guards the empty
-                        // slots and any NaN key)
+                        // that can map there.  Empty slots hold group 0 with
+                        // prefix 0x1fffff, which only a NaN key (already an
+                        // error) can match, inside group 0's bins.
                         const uint32_t pfx = key >> 10;
                         const uint32_t e = th[(pfx * hmul) >> (32 - NHASH_BITS)];
-                        const uint32_t g = e >> 21;
-                        if (valid && ((e ^ pfx) & 0x1FFFFFu) == 0u && g < nfin)  // rare
-                            atomicAdd(gbins + g * NFINE + (key & (NFINE - 1)), 1ull);
+                        if (valid && ((e ^ pfx) & 0x1FFFFFu) == 0u)  // rare
+                            atomicAdd(gbins + (e >> 21) * NFINE + (key & (NFINE - 1)), 1ull);
                     } else {
                         // t2[0] is a -1 sentinel: no branch on the first lookup
                         const int g1 = t1[c];
@@ -524,7 +523,7 @@ k_select(SelBufs sb, const SeriesDev *series, int s_begin, int K, float *eps_out
         uint32_t *fh = sb.tab_hash ? sb.tab_hash + (int64_t)s * NHASH : nullptr;
         for (int x = t; x < NCOARSE; x += THREADS) f1[x] = -1;
         for (int x = t; x < K * NFINE; x += THREADS) f2[x] = -1;
-        for (int x = t; fh && x < NHASH; x += THREADS) fh[x] = 0xffffffffu;
+        for (int x = t; fh && x < NHASH; x += THREADS) fh[x] = 0x1fffffu;  // group 0, no finite key
         __syncthreads();
         if (t == 0) {
             int g1 = 0, g = 0;

@@ -191,3 +191,31 @@ def test_phase_times_on_replay(rqa_lib):
         assert np.all(ms >= 0) and ms[4] > 0, ms  # the line pass takes time
     assert rqa.rqa_graph_replays(ctx) == 2
     ctx.close()
+
+
+def test_replay_with_learned_bracket(rqa_lib):
+    """The bench configuration: batched schedule, learned bracket, one call
+    replayed; bit-identical to a radix-selection run without graphs and to
+    the oracle."""
+    import os
+    import torch
+    rqa = rqa_lib
+    from paper_2208_09136_gb300 import bracket
+    if not os.path.exists(bracket.MODEL_PATH):
+        pytest.skip("no trained model file")
+    stream = torch.cuda.Stream()
+    ys = _series(31, [3000, 700, 5000, 150])
+    ctx = rqa.Context(stream=stream, select=rqa.RQA_SELECT_BRACKET)
+    bracket.install(ctx)
+    run = _Run(rqa, ctx, ys, 3, 3, stream)
+    first = run.call()
+    for _ in range(2):
+        _same(run.call(), first)
+    assert rqa.rqa_graph_replays(ctx) == 2
+    hits, misses = rqa.rqa_bracket_stats(ctx)
+    assert hits + misses == len(ys) * 20
+    ref_ctx = rqa.Context(stream=stream, select=rqa.RQA_SELECT_RADIX, flags=rqa.RQA_FLAG_NO_GRAPHS)
+    _same(_Run(rqa, ref_ctx, ys, 3, 3, stream).call(), first)
+    _against_oracle(first, ys, 3, 3)
+    ctx.close()
+    ref_ctx.close()
