@@ -27,6 +27,7 @@ namespace rqa {
 // WSH+1..LSH go straight to the series' global short histogram and longer
 // ones to the caller's full histogram (both rare).
 constexpr int WSH = 48;
+static_assert(WSH >= 30, "lines inside one 32-cell word must fit the warp histogram");
 
 template <bool HIST>
 struct LineSink {
@@ -55,6 +56,8 @@ struct LineSink {
             longmass += len;
         }
     }
+    // a line strictly inside one 32-cell word: 4 <= len <= 30 < WSH
+    __device__ __forceinline__ void emit_interior(uint32_t len) { atomicAdd(&hs[len * 32u], 1u); }
     // fold the popcount tallies into the histogram column
     __device__ __forceinline__ void settle()
     {
@@ -114,7 +117,7 @@ __device__ __forceinline__ void runs_word(uint32_t w, uint32_t &c, Sink &sink)
     sink.cp += n1 + n2 * 1023u + n3 * 0xFFC00u - (uint32_t)__popc(x) * 0x100000u;
     while (x) {
         const int p = __ffs(x) - 1;
-        sink.emit((uint32_t)(__ffs(~(mid >> p)) - 1));
+        sink.emit_interior((uint32_t)(__ffs(~(mid >> p)) - 1));
         x &= x - 1;
     }
 }
