@@ -11,7 +11,7 @@
  *   distance     d_ij = max_q |y[i+q tau] - y[j+q tau]|, maximum norm (Sect. 2).
  *   recurrence   R_ij = [d_ij <= eps] (Eq. 1-2; see below for the boundary).
  *   upper        only pairs i < j are used (Sect. 4); P = Ne(Ne-1)/2 pairs.
- *   RR target    rr_num/rr_den of the P pairs (Eq. 3, "preselect RR").
+ *   RR target    rr_num/rr_den of the P pairs (Eq. 3; Sect. 2 fixes RR first).
  *   eps_k        the T_k-th smallest distance, T_k = ceil(rr_num_k * P / rr_den).
  *                Cells with d <= eps_k are recurrent, so #{d < eps_k} < T_k
  *                <= #{d <= eps_k}.  (Eq. 2 has H(0) = 0; the inclusive test is
@@ -164,8 +164,8 @@ int rqa_target_counts(uint64_t P, const int32_t *rr_num, int32_t rr_den, int32_t
 /* ---- the hot path -------------------------------------------------------- */
 
 /*
- * Exact thresholds for K recurrence-rate targets per series (Sect. 2,
- * "preselect RR and use the corresponding eps"; Eq. 3).
+ * Exact thresholds for K recurrence-rate targets per series (Sect. 2: the
+ * recurrence rate is chosen first and eps is the value that yields it; Eq. 3).
  *   rr_num     host, K numerators, strictly ascending, each in 1..rr_den-1
  *   rr_den     denominator (100 for RR in per cent)
  *   eps_out    device, S*K FP32, row s = series s: eps_k is the T_k-th smallest

@@ -19,8 +19,8 @@ Readings of the paper (the paper is silent or ambiguous on these):
 * RR targets are rationals rr_num / rr_den (the paper's RR in per cent is
   rr_num / 100).  The target count is T = ceil(rr_num * P / rr_den) in exact
   integers.
-* The threshold for a target is the T-th smallest distance, eps (Sect. 2:
-  "preselect RR and use the corresponding value for eps").  A cell is
+* The threshold for a target is the T-th smallest distance, eps (Sect. 2
+  fixes the recurrence rate first and takes the eps that yields it).  A cell is
   recurrent iff d_ij <= eps.  (Eq. 2 sets H(0) = 0, i.e. strict d < eps; the
   inclusive form is Eq. 1 evaluated at the next float above eps, and is the
   only reading under which an all-equal-distance series has any recurrence.)
@@ -79,7 +79,7 @@ def all_distances(y: np.ndarray, m: int, tau: int) -> np.ndarray:
 
 def eps_for_rr(y: np.ndarray, m: int, tau: int, rr_num: Sequence[int], rr_den: int,
                dist: np.ndarray = None) -> Dict[str, np.ndarray]:
-    """Exact thresholds by sorting all distances (Sect. 2, "preselect RR").
+    """Exact thresholds by sorting all distances (Sect. 2: RR fixed first, eps from it).
 
     Returns eps (FP32), T, count_le = #{d <= eps}, count_lt = #{d < eps}.
     """

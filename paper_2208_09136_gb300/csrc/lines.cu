@@ -4,8 +4,8 @@
 //
 // A warp owns a band of D consecutive diagonals and walks down it 32 rows at
 // a time.  For each diagonal of the band, lane t computes the distance of
-// cell (i0+t, i0+t+delta) and its rank r = #{k : eps_k < d} (a 5-step
-// branch-free search over the sorted thresholds, padded to 32).  Five
+// cell (i0+t, i0+t+delta) and its rank r = #{k : eps_k < d} (one lookup in
+// a bucket table of the thresholds, or a 5-step search over them).  Five
 // __ballot_sync calls publish the bit planes of r to the warp; lane k then
 // rebuilds its own 32-cell recurrence word {t : r_t <= k} with a bit-sliced
 // comparison, and reads its runs with __ffs/__clz/popc bit tricks.  The run
@@ -13,9 +13,10 @@
 // 32 rows.  So all K thresholds share one distance evaluation per cell, and
 // the bitmask work per cell is spread over K lanes.
 //
-// Outputs per (series, threshold): C_k = recurrent cells (popc of the words),
-// P_k(l) for l <= LSH in shared memory (flushed once per work item), longer
-// lines straight to the caller's full histogram, and L_max.
+// Outputs per (series, threshold): P_k(l) (lengths up to WSH in a per-warp
+// shared histogram flushed once per work unit, WSH+1..LSH in the series'
+// global short histogram, longer lines straight to the caller's full
+// histogram), L_max, and C_k = sum of l P_k(l), the recurrent cells.
 #include <cstdint>
 #include <type_traits>
 #include "rqa_common.cuh"

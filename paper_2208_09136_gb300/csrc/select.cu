@@ -1,5 +1,5 @@
-// Exact selection of the RR-preselected thresholds (Sect. 2, "preselect RR
-// and use the corresponding value for eps"; Eq. 3).
+// Exact selection of the thresholds that give the chosen recurrence rates
+// (Sect. 2: RR is fixed first and eps follows from it; Eq. 3).
 //
 // eps_k is the T_k-th smallest upper-triangle distance.  Distances are never
 // stored: every counting round recomputes them over diagonal bands and
