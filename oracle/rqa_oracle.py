@@ -170,6 +170,44 @@ def det_avg(det: np.ndarray) -> np.ndarray:
     return acc / np.float64(k)
 
 
+def line_measures(hist: np.ndarray, lmin: Sequence[int]) -> Dict[str, np.ndarray]:
+    """Average diagonal line length L and line-length entropy ENTR (K, len(lmin)).
+
+    Sect. 2 closes by noting that the averaging over RR applies to other RQA
+    measures as well; these two are the usual diagonal-line measures next to
+    DET (Marwan et al. 2007, Phys. Rep. 438, Sect. 5.1), over lines of length
+    >= lmin of the upper triangle (both triangles hold the same lines, so the
+    ratios equal the full-matrix ones without the line of identity):
+        N_l  = sum_{l >= lmin} P(l)                  (number of lines)
+        L    = sum_{l >= lmin} l P(l) / N_l          (FP64 ratio of exact integers;
+                                                      NaN when N_l = 0)
+        ENTR = -sum_{l >= lmin} p(l) ln p(l),  p(l) = P(l) / N_l
+               (natural logarithm, FP64, summed over l ascending; 0 when N_l = 0).
+    """
+    k, nl = hist.shape
+    L = np.zeros((k, len(lmin)), dtype=np.float64)
+    E = np.zeros((k, len(lmin)), dtype=np.float64)
+    for kk in range(k):
+        row = [int(v) for v in hist[kk]]
+        for j, lm in enumerate(lmin):
+            n_lines = sum(c for l, c in enumerate(row, start=1) if l >= lm)
+            mass = sum(l * c for l, c in enumerate(row, start=1) if l >= lm)
+            L[kk, j] = float(mass) / float(n_lines) if n_lines else float("nan")
+            ent = 0.0
+            for l, c in enumerate(row, start=1):
+                if l >= lm and c:
+                    pl = float(c) / float(n_lines)
+                    ent = ent - pl * float(np.log(pl))
+            E[kk, j] = ent
+    return {"L": L, "entr": E}
+
+
+def measure_avg(v: np.ndarray) -> np.ndarray:
+    """Average of a per-target measure over the K targets (the same reduction
+    as Eq. avgDET): FP64 sum in k order, then / K."""
+    return det_avg(v)
+
+
 def rqa_det_avg(y: np.ndarray, m: int, tau: int, rr_num: Sequence[int], rr_den: int,
                 lmin: Sequence[int] = (2,)) -> Dict[str, np.ndarray]:
     """The whole hot path on one series: eps_k, line statistics, DET_k, mean."""

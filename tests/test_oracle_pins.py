@@ -274,3 +274,67 @@ def test_c_oracle_agrees_with_numpy_oracle(n, m, tau):
     for key in ("hist", "count", "stencil", "lmax"):
         assert np.array_equal(L[key], r[key]), key
     assert np.array_equal(L["short_hist"], r["hist"][:, :8])
+
+
+# ------------------------------------------------------------- L and ENTR
+def test_line_measures_closed_forms():
+    """L and ENTR on histograms with known answers: one length only (ENTR 0,
+    L that length), equal counts of n lengths (ENTR ln n), lmin above every
+    line (L NaN, ENTR 0), and a worked mixture."""
+    K = 1
+    h = np.zeros((K, 20), dtype=np.uint64)
+    h[0, 6] = 5                                   # five lines of length 7
+    r = O.line_measures(h, [1, 2, 7, 8])
+    assert list(r["L"][0, :3]) == [7.0, 7.0, 7.0] and math.isnan(r["L"][0, 3])
+    assert list(r["entr"][0]) == [0.0, 0.0, 0.0, 0.0]
+    h = np.zeros((1, 10), dtype=np.uint64)
+    h[0, [1, 3, 4, 8]] = 3                        # lengths 2, 4, 5, 9, three each
+    r = O.line_measures(h, [1, 3, 6])
+    assert r["entr"][0, 0] == pytest.approx(math.log(4), rel=1e-15)
+    assert r["entr"][0, 1] == pytest.approx(math.log(3), rel=1e-15)
+    assert r["entr"][0, 2] == 0.0
+    assert r["L"][0, 0] == (2 + 4 + 5 + 9) / 4 and r["L"][0, 1] == (4 + 5 + 9) / 3
+    h = np.zeros((1, 4), dtype=np.uint64)
+    h[0, 0], h[0, 1], h[0, 3] = 2, 1, 1           # p = 1/2, 1/4, 1/4
+    r = O.line_measures(h, [1])
+    assert r["entr"][0, 0] == pytest.approx(1.5 * math.log(2), rel=1e-15)
+    assert r["L"][0, 0] == (2 * 1 + 2 + 4) / 4
+
+
+@pytest.mark.parametrize("n,m,tau", [(40, 1, 1), (31, 3, 2)])
+def test_line_measures_constant_series(n, m, tau):
+    """Constant series: one line of every length 1..Ne-1 (the upper triangle's
+    diagonals are all fully recurrent), so for lines >= lmin:
+    L = mean of lmin..Ne-1 and ENTR = ln(Ne - lmin)."""
+    y = np.full(n, 0.75, dtype=np.float32)
+    ne = n - (m - 1) * tau
+    res = O.rqa_det_avg(y, m, tau, [1, 50], 100, (2,))
+    lm = [1, 2, 5]
+    r = O.line_measures(res["hist"], lm)
+    for j, l0 in enumerate(lm):
+        ls = list(range(l0, ne))
+        assert r["L"][0, j] == pytest.approx(sum(ls) / len(ls), rel=1e-15)
+        assert r["entr"][0, j] == pytest.approx(math.log(len(ls)), rel=1e-13)
+
+
+@pytest.mark.parametrize("seed,n,m,tau", [(1, 17, 2, 1), (4, 33, 3, 3)])
+def test_line_measures_full_matrix_brute_force(seed, n, m, tau):
+    """L and ENTR from the full ordered-pair matrix (every line counted twice,
+    by pure-Python run scanning) equal the oracle's upper-triangle values."""
+    rng = np.random.default_rng(seed)
+    y = (rng.integers(0, 6, size=n) * 0.25).astype(np.float32) if seed % 2 else \
+        rng.standard_normal(n).astype(np.float32)
+    rr_num, lmin = [5, 20, 50], (1, 2, 3)
+    orc = O.rqa_det_avg(y, m, tau, rr_num, 100, lmin)
+    r = O.line_measures(orc["hist"], lmin)
+    for k, b in enumerate(_brute_full(y, m, tau, rr_num, 100, lmin)):
+        h2 = b["hist2"]
+        for j, lm in enumerate(lmin):
+            nl = sum(h2[l] for l in range(lm, len(h2)))
+            if nl == 0:
+                assert math.isnan(r["L"][k, j]) and r["entr"][k, j] == 0.0
+                continue
+            L2 = sum(l * h2[l] for l in range(lm, len(h2))) / nl
+            E2 = -sum((h2[l] / nl) * math.log(h2[l] / nl) for l in range(lm, len(h2)) if h2[l])
+            assert r["L"][k, j] == pytest.approx(L2, rel=1e-15)
+            assert r["entr"][k, j] == pytest.approx(E2, rel=1e-13, abs=1e-15)
