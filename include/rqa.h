@@ -225,6 +225,30 @@ int rqa_line_hist(rqa_ctx *ctx, const rqa_batch *batch, const float *eps, int32_
                   uint64_t *hist, const int64_t *hist_offsets, uint32_t *lmax,
                   uint64_t *count, uint64_t *stencil);
 
+/*
+ * Other diagonal-line measures from the same histograms, averaged over the
+ * targets like DET (Sect. 2 ends by noting that the averaging applies to
+ * other RQA measures; these are the two usually reported next to DET):
+ *   N_l  = sum_{l >= lmin} P_k(l)                 lines of length >= lmin
+ *   L    = sum_{l >= lmin} l P_k(l) / N_l         average line length, FP64
+ *                                                 ratio of exact integers; NaN
+ *                                                 when N_l = 0
+ *   ENTR = -sum_{l >= lmin} p ln p, p = P_k(l)/N_l  line-length entropy, FP64,
+ *                                                 natural log; 0 when N_l = 0
+ *   hist, hist_offsets  a full histogram as written by rqa_line_hist or
+ *                rqa_det_avg (device; host offsets, checked like theirs)
+ *   lmin         host, n_lmin (1..RQA_LMIN_MAX) minimal lengths, each >= 1
+ *   L_out, entr_out   device, S*K*n_lmin FP64, [s][k][j] (may be NULL)
+ *   L_avg, entr_avg   device, S*n_lmin FP64: the mean over k, summed in k
+ *                order then divided by K (may be NULL; computed in context
+ *                scratch when the per-target array is NULL)
+ * Asynchronous on the context's stream; the histogram must be complete when
+ * the stream reaches this call.
+ */
+int rqa_line_measures(rqa_ctx *ctx, const rqa_batch *batch, int32_t K, const uint64_t *hist,
+                      const int64_t *hist_offsets, const int32_t *lmin, int32_t n_lmin,
+                      double *L_out, double *entr_out, double *L_avg, double *entr_avg);
+
 /* ---- selection without allocation ---------------------------------------
  *
  * The paper has no counterpart to this entry point; it exists for callers

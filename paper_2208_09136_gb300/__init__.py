@@ -21,7 +21,7 @@ from .abi import (  # noqa: F401
     rqa_sketch, rqa_mlp_forward, rqa_mlp_backward, rqa_adam_step, rqa_set_bracket_model,
     rqa_bracket_stats, RQA_MLP_PARAMS, RQA_MLP_ACTS, RQA_MLP_OUT,
     rqa_eps_for_rr_noalloc, RQA_NOALLOC_MAX_SERIES,
-    rqa_graph_replays, rqa_autotune, RQA_FLAG_NO_GRAPHS,
+    rqa_graph_replays, rqa_autotune, RQA_FLAG_NO_GRAPHS, rqa_line_measures,
     RQA_SCHED_BATCHED, RQA_SCHED_PER_SERIES, RQA_SELECT_AUTO, RQA_SELECT_BRACKET,
     RQA_SELECT_RADIX, RQA_K_MAX, RQA_LMIN_MAX, RQA_FEATURES,
 )
@@ -63,6 +63,22 @@ def det_avg(ctx: Context, batch: Batch, rr_num: Optional[Sequence[int]], rr_den:
                     out["lmax"], out["count"], out["stencil"])
     else:
         rqa_det_avg(ctx, batch, rr_num, rr_den, eps, K, lmin, det, avg, used)
+    return out
+
+
+def line_measures(ctx: Context, batch: Batch, hist, hist_offsets, K: int,
+                  lmin: Sequence[int] = (2,)) -> Dict[str, "object"]:
+    """Average line length L and line-length entropy ENTR per target (S, K, L)
+    and their means over the targets (S, L), from a full line histogram."""
+    import torch
+    S = batch.n_series
+    dev = batch.y.device
+    out = {"L": torch.empty((S, K, len(lmin)), dtype=torch.float64, device=dev),
+           "entr": torch.empty((S, K, len(lmin)), dtype=torch.float64, device=dev),
+           "L_avg": torch.empty((S, len(lmin)), dtype=torch.float64, device=dev),
+           "entr_avg": torch.empty((S, len(lmin)), dtype=torch.float64, device=dev)}
+    rqa_line_measures(ctx, batch, K, hist, hist_offsets, lmin, out["L"], out["entr"], out["L_avg"],
+                      out["entr_avg"])
     return out
 
 

@@ -72,6 +72,8 @@ _SIGS = {
     "rqa_phase_times": ([c_vp, c_vp, c_int], c_int),
     "rqa_kernel_launches": ([c_vp], c_u64),
     "rqa_graph_replays": ([c_vp], c_u64),
+    "rqa_line_measures": ([c_vp, ctypes.POINTER(_Batch), c_i32, c_vp, c_vp, c_vp, c_i32, c_vp, c_vp,
+                           c_vp, c_vp], c_int),
     "rqa_autotune": ([c_vp, ctypes.POINTER(_Batch), c_vp, c_i32, c_i32, c_vp], c_int),
     "rqa_line_hist": ([c_vp, ctypes.POINTER(_Batch), c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp],
                       c_int),
@@ -296,6 +298,24 @@ def rqa_phase_times(ctx: Context) -> np.ndarray:
 
 def rqa_kernel_launches(ctx: Context) -> int:
     return int(lib().rqa_kernel_launches(ctx.handle))
+
+
+def rqa_line_measures(ctx: Context, batch: Batch, K: int, hist, hist_offsets, lmin, L_out=None,
+                      entr_out=None, L_avg=None, entr_avg=None):
+    import torch
+    S = batch.n_series
+    lm = np.ascontiguousarray(lmin, dtype=np.int32)
+    hoff = np.ascontiguousarray(hist_offsets, dtype=np.int64)
+    b = batch._c()
+    n = S * K * len(lm)
+    _check(lib().rqa_line_measures(ctx.handle, ctypes.byref(b), int(K),
+                                   _dev_ptr(hist, torch.uint64, int(hoff[-1]), "hist"), _np_ptr(hoff),
+                                   _np_ptr(lm), len(lm),
+                                   _dev_ptr(L_out, torch.float64, n, "L_out"),
+                                   _dev_ptr(entr_out, torch.float64, n, "entr_out"),
+                                   _dev_ptr(L_avg, torch.float64, S * len(lm), "L_avg"),
+                                   _dev_ptr(entr_avg, torch.float64, S * len(lm), "entr_avg")),
+           "rqa_line_measures")
 
 
 def rqa_graph_replays(ctx: Context) -> int:

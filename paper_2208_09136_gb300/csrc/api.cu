@@ -64,6 +64,7 @@ struct rqa_ctx {
         redo;
     DevBuf queue, status;
     DevBuf eps_tmp, le_tmp, lt_tmp, count, lmax, hshort;
+    DevBuf meas;  // per-target L / ENTR when only their averages are asked for
 
     // learned bracket
     DevBuf mlp;                 // installed network parameters
@@ -740,7 +741,7 @@ void rqa_destroy(rqa_ctx *c)
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->arena, &c->prefix, &c->level, &c->rank, &c->below, &c->tab_sub,
                       &c->tab_mid, &c->tab_fin1, &c->tab_fin2, &c->tab_hash, &c->ngroups, &c->hist,
-                      &c->krange,
+                      &c->krange, &c->meas,
                       &c->redo,
                       &c->queue,
                       &c->status, &c->eps_tmp, &c->le_tmp, &c->lt_tmp, &c->count, &c->lmax,
@@ -931,6 +932,32 @@ int rqa_line_hist(rqa_ctx *c, const rqa_batch *b, const float *eps, int32_t K, u
     if (int rc = line_outputs_tail(c, pl, &lo, lb)) return rc;
     mark(c, 6);
     return RQA_OK;
+}
+
+int rqa_line_measures(rqa_ctx *c, const rqa_batch *b, int32_t K, const uint64_t *hist,
+                      const int64_t *hist_offsets, const int32_t *lmin, int32_t n_lmin, double *L_out,
+                      double *entr_out, double *L_avg, double *entr_avg)
+{
+    if (!c || !hist || !lmin || n_lmin < 1 || n_lmin > RQA_LMIN_MAX || K < 1 || K > RQA_K_MAX)
+        return RQA_ERR_INVALID_ARG;
+    for (int j = 0; j < n_lmin; ++j)
+        if (lmin[j] < 1) return RQA_ERR_INVALID_ARG;
+    if (int rc = validate_batch(b)) return rc;
+    if (int rc = validate_hist(b, K, hist, hist_offsets)) return rc;
+    if (!L_out && !entr_out && !L_avg && !entr_avg) return RQA_OK;
+    cudaSetDevice(c->device);
+    Plan pl;
+    if (int rc = make_plan(c, b, nullptr, 0, K, pl)) return rc;
+    const size_t n = (size_t)pl.S * K * n_lmin;
+    double *L = L_out, *E = entr_out;
+    if ((L_avg && !L) || (entr_avg && !E)) {
+        if (int rc = ensure(c->meas, 2 * n * sizeof(double))) return rc;
+        if (L_avg && !L) L = P<double>(c->meas);
+        if (entr_avg && !E) E = P<double>(c->meas) + n;
+    }
+    if (int rc = upload_plan(c, pl, lmin, n_lmin, hist_offsets)) return rc;
+    return launched(c, launch_line_measures(hist, pl.d_hoff, pl.S, K, pl.d_lmin, n_lmin, L, E, L_avg,
+                                            entr_avg, c->stream));
 }
 
 int rqa_set_timing(rqa_ctx *c, int enable)

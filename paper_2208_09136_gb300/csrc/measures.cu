@@ -1,0 +1,121 @@
+// Average diagonal line length L and line-length entropy ENTR per target, and
+// their averages over the targets.  Sect. 2 ends by noting that averaging over
+// a range of recurrence rates applies to other RQA measures than DET; these
+// are the two diagonal-line measures usually reported with it (Marwan et al.
+// 2007, Phys. Rep. 438, Sect. 5.1), over lines of length >= lmin:
+//   N_l  = sum_{l >= lmin} P(l),  L = sum_{l >= lmin} l P(l) / N_l,
+//   ENTR = -sum_{l >= lmin} p(l) ln p(l),  p(l) = P(l) / N_l.
+// The input is the full histogram the line pass wrote (upper triangle; both
+// triangles hold the same lines, so the ratios equal the full-matrix ones).
+#include <cstdint>
+#include "rqa_common.cuh"
+
+namespace rqa {
+
+constexpr int MT = 256;  // threads per (series, target)
+
+// One CTA per (series s, target k): integer sums first (exact in any order),
+// then the entropy terms in FP64 (a fixed reduction tree).
+__global__ void __launch_bounds__(MT)
+k_line_measures(const uint64_t *__restrict__ hist, const int64_t *__restrict__ hoff, int K,
+                const int32_t *__restrict__ lmin, int n_lmin, double *L_out, double *E_out)
+{
+    __shared__ unsigned long long red_n[MT / 32][LMIN_MAX], red_m[MT / 32][LMIN_MAX];
+    __shared__ double red_e[MT / 32][LMIN_MAX];
+    __shared__ unsigned long long tot_n[LMIN_MAX];
+    const int s = blockIdx.x / K, k = blockIdx.x - s * K;
+    const int64_t nl = (hoff[s + 1] - hoff[s]) / K;  // lengths 1..nl
+    const uint64_t *row = hist + hoff[s] + (int64_t)k * nl;
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+
+    unsigned long long n[LMIN_MAX], m[LMIN_MAX];
+#pragma unroll
+    for (int j = 0; j < LMIN_MAX; ++j) n[j] = m[j] = 0ull;
+    for (int64_t l = 1 + t; l <= nl; l += MT) {
+        const unsigned long long c = row[l - 1];
+        if (!c) continue;
+#pragma unroll
+        for (int j = 0; j < LMIN_MAX; ++j)
+            if (j < n_lmin && l >= lmin[j]) {
+                n[j] += c;
+                m[j] += c * (unsigned long long)l;
+            }
+    }
+#pragma unroll
+    for (int j = 0; j < LMIN_MAX; ++j) {
+        for (int o = 16; o > 0; o >>= 1) {
+            n[j] += __shfl_xor_sync(FULL, n[j], o);
+            m[j] += __shfl_xor_sync(FULL, m[j], o);
+        }
+        if (lane == 0) {
+            red_n[w][j] = n[j];
+            red_m[w][j] = m[j];
+        }
+    }
+    __syncthreads();
+    if (t < n_lmin) {
+        unsigned long long sn = 0, sm = 0;
+        for (int q = 0; q < MT / 32; ++q) {
+            sn += red_n[q][t];
+            sm += red_m[q][t];
+        }
+        tot_n[t] = sn;
+        if (L_out)
+            L_out[((int64_t)s * K + k) * n_lmin + t] =
+                sn ? (double)sm / (double)sn : __longlong_as_double(0x7ff8000000000000ll);
+    }
+    __syncthreads();
+    if (!E_out) return;
+    double e[LMIN_MAX];
+#pragma unroll
+    for (int j = 0; j < LMIN_MAX; ++j) e[j] = 0.0;
+    for (int64_t l = 1 + t; l <= nl; l += MT) {
+        const unsigned long long c = row[l - 1];
+        if (!c) continue;
+#pragma unroll
+        for (int j = 0; j < LMIN_MAX; ++j)
+            if (j < n_lmin && l >= lmin[j]) {
+                const double p = (double)c / (double)tot_n[j];
+                e[j] -= p * log(p);
+            }
+    }
+#pragma unroll
+    for (int j = 0; j < LMIN_MAX; ++j) {
+        for (int o = 16; o > 0; o >>= 1) e[j] += __shfl_xor_sync(FULL, e[j], o);
+        if (lane == 0) red_e[w][j] = e[j];
+    }
+    __syncthreads();
+    if (t < n_lmin) {
+        double se = 0.0;
+        for (int q = 0; q < MT / 32; ++q) se += red_e[q][t];
+        E_out[((int64_t)s * K + k) * n_lmin + t] = se;
+    }
+}
+
+// Averages over the K targets of one series: FP64 sum in k order, then / K
+// (the reduction of Eq. avgDET).
+__global__ void k_measure_avg(const double *v, int K, int n_lmin, double *avg)
+{
+    const int s = blockIdx.x, j = threadIdx.x;
+    if (j >= n_lmin) return;
+    double acc = 0.0;
+    for (int k = 0; k < K; ++k) acc = acc + v[((int64_t)s * K + k) * n_lmin + j];
+    avg[(int64_t)s * n_lmin + j] = acc / (double)K;
+}
+
+cudaError_t launch_line_measures(const uint64_t *hist, const int64_t *hoff_dev, int S, int K,
+                                 const int32_t *lmin_dev, int n_lmin, double *L_out,
+                                 double *E_out, double *L_avg, double *E_avg, cudaStream_t st)
+{
+    if (!hist || !hoff_dev || !lmin_dev || S < 1 || K < 1 || K > KMAX || n_lmin < 1 ||
+        n_lmin > LMIN_MAX || (L_avg && !L_out) || (E_avg && !E_out))
+        return cudaErrorInvalidValue;
+    k_line_measures<<<S * K, MT, 0, st>>>(hist, hoff_dev, K, lmin_dev, n_lmin, L_out, E_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (L_avg) k_measure_avg<<<S, 32, 0, st>>>(L_out, K, n_lmin, L_avg);
+    if (E_avg) k_measure_avg<<<S, 32, 0, st>>>(E_out, K, n_lmin, E_avg);
+    return cudaGetLastError();
+}
+
+}  // namespace rqa
