@@ -21,6 +21,8 @@
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
+
+#define ORC_KMAX 128 /* thresholds per call (capacity of the per-thread arrays) */
 #endif
 
 static inline float orc_dist(const float *y, int64_t i, int64_t j, int m, int tau)
@@ -52,7 +54,7 @@ int orc_distances(const float *y, int64_t n, int m, int tau, float *out)
 int orc_count(const float *y, int64_t n, int m, int tau, const float *thr, int K,
               uint64_t *le, uint64_t *lt, int threads)
 {
-    if (K < 1 || K > 64) return -1;
+    if (K < 1 || K > ORC_KMAX) return -1;
     int64_t ne = n - (int64_t)(m - 1) * tau;
     for (int k = 0; k < K; ++k) { le[k] = 0; lt[k] = 0; }
 #ifdef _OPENMP
@@ -60,7 +62,7 @@ int orc_count(const float *y, int64_t n, int m, int tau, const float *thr, int K
 #pragma omp parallel
 #endif
     {
-        uint64_t ple[64], plt[64];
+        uint64_t ple[ORC_KMAX], plt[ORC_KMAX];
         for (int k = 0; k < K; ++k) { ple[k] = 0; plt[k] = 0; }
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 16)
@@ -97,7 +99,7 @@ int orc_lines(const float *y, int64_t n, int m, int tau, const float *eps, int K
               uint64_t *hist, uint64_t *count, uint64_t *stencil, uint32_t *lmax,
               uint64_t *short_hist, int n_short, int threads)
 {
-    if (K < 1 || K > 64) return -1;
+    if (K < 1 || K > ORC_KMAX) return -1;
     int64_t ne = n - (int64_t)(m - 1) * tau;
     int64_t nl = ne - 1;
     if (hist) memset(hist, 0, sizeof(uint64_t) * (size_t)K * (size_t)(nl > 0 ? nl : 0));
@@ -108,9 +110,9 @@ int orc_lines(const float *y, int64_t n, int m, int tau, const float *eps, int K
 #pragma omp parallel
 #endif
     {
-        uint64_t pc[64], ps[64];
-        uint32_t pm[64];
-        int64_t run[64];
+        uint64_t pc[ORC_KMAX], ps[ORC_KMAX];
+        uint32_t pm[ORC_KMAX];
+        int64_t run[ORC_KMAX];
         uint64_t *ph = NULL;
         uint64_t *psh = NULL;
         if (hist) ph = (uint64_t *)calloc((size_t)K * (size_t)nl, sizeof(uint64_t));
@@ -122,7 +124,7 @@ int orc_lines(const float *y, int64_t n, int m, int tau, const float *eps, int K
         for (int64_t dl = 1; dl < ne; ++dl) {
             int64_t len = ne - dl;
             for (int k = 0; k < K; ++k) run[k] = 0;
-            int prev_rec[64];
+            int prev_rec[ORC_KMAX];
             for (int k = 0; k < K; ++k) prev_rec[k] = 0;
             float dn = (len > 0) ? orc_dist(y, 0, dl, m, tau) : 0.0f;
             for (int64_t i = 0; i <= len; ++i) {

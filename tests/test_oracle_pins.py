@@ -276,6 +276,17 @@ def test_c_oracle_agrees_with_numpy_oracle(n, m, tau):
     assert np.array_equal(L["short_hist"], r["hist"][:, :8])
 
 
+def test_c_oracle_many_targets():
+    """RR = 1..99 and 1..127 of 128 (the targets a call may hold): the C scans
+    equal the NumPy oracle's for every target."""
+    y = _series("logistic", 150, 5)
+    for rr, den in ((list(range(1, 100)), 100), (list(range(1, 128)), 128)):
+        r = O.rqa_det_avg(y, 2, 1, rr, den)
+        L = CO.lines(y, 2, 1, r["eps"], full_hist=True)
+        for key in ("hist", "count", "stencil", "lmax"):
+            assert np.array_equal(L[key], r[key]), (den, key)
+
+
 # ------------------------------------------------------------- L and ENTR
 def test_line_measures_closed_forms():
     """L and ENTR on histograms with known answers: one length only (ENTR 0,
