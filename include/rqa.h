@@ -32,7 +32,11 @@
  *     (non-finite input, unsorted thresholds, capacity, time-outs) are
  *     reported by rqa_status().
  *   - A context is not thread safe; use one per host thread.
- *   - K (number of thresholds per series) is 1 .. RQA_K_MAX.
+ *   - K (number of thresholds per series) is 1 .. RQA_K_MAX, so a call can
+ *     average over RR = 1..99 % (Sect. 2 considers RR* up to 99).  The line
+ *     pass handles up to 31 thresholds per sweep over the cells; a call with
+ *     larger K makes ceil(K / 31) sweeps (same results, proportionally
+ *     slower line pass).
  *   - A series must have Ne >= 2 (P >= 1), otherwise RQA_ERR_TOO_SHORT.
  */
 #ifndef RQA_H
@@ -46,7 +50,7 @@ extern "C" {
 #endif
 
 #define RQA_ABI_VERSION 1
-#define RQA_K_MAX 31          /* thresholds per series and call */
+#define RQA_K_MAX 127         /* thresholds per series and call */
 #define RQA_M_MAX 16          /* embedding dimension */
 #define RQA_LMIN_MAX 8        /* entries of the lmin list of rqa_det_avg */
 #define RQA_SKETCH_PAIRS 4096 /* random pairs of the distance sketch */
@@ -272,10 +276,12 @@ int rqa_line_measures(rqa_ctx *ctx, const rqa_batch *batch, int32_t K, const uin
  *     count_le / count_lt may be NULL.
  *   - status_out: device int (may be NULL) that receives the device-side
  *     status of the call (RQA_OK, RQA_ERR_NONFINITE, ...) when it completes.
+ *   - K is at most RQA_NOALLOC_K_MAX here (RQA_ERR_INVALID_ARG above).
  *   - Returns RQA_ERR_CAPACITY for more than RQA_NOALLOC_MAX_SERIES series,
  *     and the argument errors of rqa_eps_for_rr; nothing is enqueued then.
  */
 #define RQA_NOALLOC_MAX_SERIES 4
+#define RQA_NOALLOC_K_MAX 31
 #define RQA_NOALLOC_SCRATCH_BYTES 1310720 /* 1.25 MiB */
 int rqa_eps_for_rr_noalloc(const rqa_batch *batch, const int32_t *rr_num, int32_t rr_den,
                            int32_t K, float *eps_out, uint64_t *count_le, uint64_t *count_lt,

@@ -23,7 +23,8 @@ c_vp = ctypes.c_void_p
 
 RQA_SCHED_BATCHED, RQA_SCHED_PER_SERIES = 0, 1
 RQA_SELECT_AUTO, RQA_SELECT_RADIX, RQA_SELECT_BRACKET = 0, 1, 2
-RQA_K_MAX = 31
+RQA_K_MAX = 127
+RQA_NOALLOC_K_MAX = 31
 RQA_LMIN_MAX = 8
 RQA_FEATURES = 131
 RQA_MLP_HIDDEN = 256

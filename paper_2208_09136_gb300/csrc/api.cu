@@ -402,6 +402,7 @@ SelBufs sel_bufs(rqa_ctx *c, const Plan &pl)
     sb.tab_mid = P<int8_t>(c->tab_mid);
     sb.tab_fin1 = P<int8_t>(c->tab_fin1);
     sb.tab_fin2 = P<int8_t>(c->tab_fin2);
+    sb.fin2_stride = (int64_t)KMAX * NFINE;
     int32_t *ng = P<int32_t>(c->ngroups);
     sb.n_sub = ng;
     sb.n_mid = ng + pl.S;
@@ -417,6 +418,12 @@ SelBufs sel_bufs(rqa_ctx *c, const Plan &pl)
 
 
 // Zero the queue tickets of n launches; returns the first ticket pointer.
+// Counting launches of one selection (per series in the per-series
+// schedule): bracket/coarse, middle rounds of MID_GROUPS groups, final.
+int select_launches(int K) { return 3 + (K + MID_GROUPS - 1) / MID_GROUPS; }
+// Line-pass launches: groups of at most LINE_KMAX targets.
+int line_groups(int K) { return (K + LINE_KMAX - 1) / LINE_KMAX; }
+
 int reset_queue(rqa_ctx *c, int n, unsigned **q)
 {
     if (int rc = ensure(c->queue, (size_t)n * 64)) return rc;
@@ -465,9 +472,15 @@ int run_select(rqa_ctx *c, const Plan &pl, const SelBufs &sb, const Item *items,
     const int rounds[4] = {R_COARSE_SUB, R_COARSE, R_MID, R_FINAL};
     for (int r = bracket ? 0 : 1; r < 4; ++r) {
         if (int rc = check_cuda(cudaMemsetAsync(hbase, 0, hbytes, c->stream))) return rc;
-        a.queue = q;
-        q += 16;
-        if (int rc = launched(c, launch_count(rounds[r], a, sb, K, grid, pl.mt, c->stream))) return rc;
+        // the middle round counts at most MID_GROUPS groups per launch
+        for (int g0 = 0; g0 == 0 || (rounds[r] == R_MID && g0 < K); g0 += MID_GROUPS) {
+            a.g0 = g0;
+            a.gn = MID_GROUPS;
+            a.queue = q;
+            q += 16;
+            if (int rc = launched(c, launch_count(rounds[r], a, sb, K, grid, pl.mt, c->stream)))
+                return rc;
+        }
         if (int rc = launched(c, launch_select(rounds[r], sb, pl.d_sd, s0, ns, K, eps, le, lt,
                                                P<int>(c->status), c->stream)))
             return rc;
@@ -517,7 +530,7 @@ int select_all(rqa_ctx *c, const rqa_batch *b, Plan &pl, float *eps, uint64_t *l
         return rc;
     unsigned *q = nullptr;
     if (c->schedule == RQA_SCHED_PER_SERIES) {
-        if (int rc = reset_queue(c, 4 * pl.S, &q)) return rc;
+        if (int rc = reset_queue(c, select_launches(pl.K) * pl.S, &q)) return rc;
         for (int s = 0; s < pl.S; ++s) {
             const int ib = pl.ser_begin[s], ie = pl.ser_begin[s + 1];
             if (int rc = run_select(c, pl, sb, pl.d_ser + ib, ie - ib, s, 1, q, eps, le, lt, bracket))
@@ -525,7 +538,7 @@ int select_all(rqa_ctx *c, const rqa_batch *b, Plan &pl, float *eps, uint64_t *l
         }
         return RQA_OK;
     }
-    if (int rc = reset_queue(c, 4, &q)) return rc;
+    if (int rc = reset_queue(c, select_launches(pl.K), &q)) return rc;
     return run_select(c, pl, sb, pl.d_lpt, (int)pl.items_lpt.size(), 0, pl.S, q, eps, le, lt,
                       bracket);
 }
@@ -552,6 +565,7 @@ int run_lines(rqa_ctx *c, const Plan &pl, const float *eps, uint64_t *hist, cons
     lb.hshort = P<uint64_t>(c->hshort);
     lb.hist = hist;
     lb.hist_off = d_hoff;
+    lb.kstride = K;
     if (int rc = check_cuda(cudaMemsetAsync(lb.count, 0, sk * 8, c->stream))) return rc;
     if (int rc = check_cuda(cudaMemsetAsync(lb.lmax, 0, sk * 4, c->stream))) return rc;
     if (int rc = check_cuda(cudaMemsetAsync(lb.hshort, 0, sk * LSH * 8, c->stream))) return rc;
@@ -566,29 +580,41 @@ int run_lines(rqa_ctx *c, const Plan &pl, const float *eps, uint64_t *hist, cons
     auto grid_for = [&](int64_t units) {
         return (int)std::max<int64_t>(1, std::min<int64_t>(full_grid, (units + WARPS - 1) / WARPS));
     };
+    // targets in groups of at most LINE_KMAX (one lane each), one pass per group
+    const int ng = line_groups(K), gsz = (K + ng - 1) / ng;
+    auto launch_groups = [&]() -> int {
+        for (int g = 0; g < ng; ++g) {
+            lb.k0 = g * gsz;
+            a.queue = q;
+            q += 16;
+            if (int rc = launched(c, launch_lines(a, lb, std::min(gsz, K - lb.k0), grid_for(a.n_units),
+                                                  pl.mt, c->stream)))
+                return rc;
+        }
+        return RQA_OK;
+    };
+    int rc = RQA_OK;
     if (c->schedule == RQA_SCHED_PER_SERIES) {
-        if (int rc = reset_queue(c, S, &q)) return rc;
-        for (int s = 0; s < S; ++s) {
+        if ((rc = reset_queue(c, S * ng, &q))) return rc;
+        for (int s = 0; s < S && rc == RQA_OK; ++s) {
             a.order = pl.d_ident + s;
             a.uprefix = pl.d_uprefix1 + 2 * (size_t)s;
             a.n_pos = 1;
             a.chunk = pl.chunk1[s];
             a.n_units = pl.uprefix1[2 * (size_t)s + 1];
-            a.queue = q;
-            q += 16;
-            if (int rc = launched(c, launch_lines(a, lb, K, grid_for(a.n_units), pl.mt, c->stream)))
-                return rc;
+            rc = launch_groups();
         }
-        return RQA_OK;
+    } else {
+        if ((rc = reset_queue(c, ng, &q))) return rc;
+        a.order = pl.d_order;
+        a.uprefix = pl.d_uprefix;
+        a.n_pos = S;
+        a.chunk = pl.chunk;
+        a.n_units = pl.uprefix[S];
+        rc = launch_groups();
     }
-    if (int rc = reset_queue(c, 1, &q)) return rc;
-    a.order = pl.d_order;
-    a.uprefix = pl.d_uprefix;
-    a.n_pos = S;
-    a.chunk = pl.chunk;
-    a.n_units = pl.uprefix[S];
-    a.queue = q;
-    return launched(c, launch_lines(a, lb, K, grid_for(a.n_units), pl.mt, c->stream));
+    lb.k0 = 0;  // the finalisation kernels read all K targets
+    return rc;
 }
 
 // Line pass plus the requested outputs.  hist/hoff come from the caller.
@@ -820,7 +846,8 @@ int rqa_det_avg(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t r
         if (int rc = ensure_select_bufs(c, pl.S, K)) return rc;
     if (bracket)
         if (int rc = ensure_bracket_bufs(c, pl.S)) return rc;
-    if (int rc = ensure(c->queue, (size_t)(5 * pl.S + 8) * 64)) return rc;
+    if (int rc = ensure(c->queue, (size_t)(std::max(select_launches(K), line_groups(K)) * pl.S + 8) * 64))
+        return rc;
     const int64_t *hoff = (lo && lo->hist) ? lo->hist_offsets : nullptr;
 
     // the call's signature: every argument the launch sequence depends on

@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(LTHREADS, 7) k_lines(CellArgs a, LineBufs lb, 
         if (cur < 0) return;
         if (klane) sink.settle();
         __syncwarp();
-        uint64_t *gs = lb.hshort + ((int64_t)cur * K + lane) * LSH;
+        uint64_t *gs = lb.hshort + ((int64_t)cur * lb.kstride + lb.k0 + lane) * LSH;
         uint32_t lm = sink.lmax;
         // C_k is the line mass: sum over l of l * P_k(l) (every recurrent cell
         // lies on exactly one line of its diagonal)
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(LTHREADS, 7) k_lines(CellArgs a, LineBufs lb, 
         }
         sink.lmax = lm;
         if (klane) {
-            const int64_t o = (int64_t)cur * K + lane;
+            const int64_t o = (int64_t)cur * lb.kstride + lb.k0 + lane;
             if (cnt) atomicAdd(reinterpret_cast<unsigned long long *>(lb.count + o),
                                (unsigned long long)cnt);
             if (sink.lmax) atomicMax(lb.lmax + o, sink.lmax);
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(LTHREADS, 7) k_lines(CellArgs a, LineBufs lb, 
             uint32_t v = 0xffffffffu;   // padding: above every key
             bool ok = true;
             if (klane) {
-                v = __float_as_uint(lb.eps[(int64_t)s * K + lane]);
+                v = __float_as_uint(lb.eps[(int64_t)s * lb.kstride + lb.k0 + lane]);
                 if (v == 0x80000000u) v = 0u;                           // -0 == +0
                 if ((v & 0x80000000u) || v > 0x7f800000u) ok = false;  // negative or NaN
             }
@@ -287,8 +287,8 @@ __global__ void __launch_bounds__(LTHREADS, 7) k_lines(CellArgs a, LineBufs lb, 
                 }
             }
             if (HIST && klane)
-                sink.hist = lb.hist + lb.hist_off[s] + (int64_t)lane * (sd.ne - 1);
-            sink.gshort = lb.hshort + ((int64_t)s * K + (klane ? lane : 0)) * LSH;
+                sink.hist = lb.hist + lb.hist_off[s] + (int64_t)(lb.k0 + lane) * (sd.ne - 1);
+            sink.gshort = lb.hshort + ((int64_t)s * lb.kstride + lb.k0 + (klane ? lane : 0)) * LSH;
             __syncwarp();
         }
         if (bad) continue;
@@ -440,7 +440,8 @@ cudaError_t launch_lines(const CellArgs &a, const LineBufs &lb, int K, int grid,
     const bool hist = lb.hist != nullptr;
     if (!lines_band_ok(embed, a.band_lines)) return cudaErrorInvalidValue;
     if (!a.y || !a.series || !a.order || !a.uprefix || !a.queue || !a.status || !lb.eps ||
-        !lb.count || !lb.lmax || !lb.hshort || (hist && !lb.hist_off) || K < 1 || K > KMAX ||
+        !lb.count || !lb.lmax || !lb.hshort || (hist && !lb.hist_off) || K < 1 || K > LINE_KMAX ||
+        lb.k0 < 0 || lb.k0 + K > lb.kstride ||
         grid < 1 || a.n_units < 1 || a.n_pos < 1)
         return cudaErrorInvalidValue;
     return hist ? launch_lines_h<true>(a, lb, K, grid, embed, st)
@@ -479,7 +480,8 @@ cudaError_t launch_finalize_det(const LineBufs &lb, const SeriesDev *, int S, in
                                 const int32_t *lmin_dev, int n_lmin, double *det,
                                 double *det_avg, cudaStream_t st)
 {
-    k_finalize_det<<<S, 32, 0, st>>>(lb, K, lmin_dev, n_lmin, det, det_avg);
+    if (K < 1 || K > KMAX) return cudaErrorInvalidValue;
+    k_finalize_det<<<S, 128, 0, st>>>(lb, K, lmin_dev, n_lmin, det, det_avg);  // one thread per target
     return cudaGetLastError();
 }
 

@@ -21,24 +21,26 @@ namespace {
 
 constexpr int NA_MAX_S = RQA_NOALLOC_MAX_SERIES;
 constexpr int NA_MAX_ITEMS_PER_SERIES = 1024;
+constexpr int NA_KMAX = RQA_NOALLOC_K_MAX;  // targets per call here (one middle-round launch)
+static_assert(NA_KMAX < MID_GROUPS && NA_KMAX >= NSUB_MAX, "fixed-scratch layout assumptions");
 
 // Layout of the fixed scratch array (byte offsets, 256-aligned blocks).
 constexpr size_t al(size_t x) { return (x + 255) & ~size_t(255); }
-constexpr int64_t NA_HSTRIDE = NCOARSE + (int64_t)KMAX * NFINE;  // KMAX >= NSUB_MAX
+constexpr int64_t NA_HSTRIDE = NCOARSE + (int64_t)NA_KMAX * NFINE;  // NA_KMAX >= NSUB_MAX
 constexpr size_t O_STATUS = 0;
 constexpr size_t O_QUEUE = O_STATUS + 256;
 constexpr size_t O_SERIES = O_QUEUE + 256;
 constexpr size_t O_T = O_SERIES + al(sizeof(SeriesDev) * NA_MAX_S);
-constexpr size_t O_ITEMS = O_T + al(sizeof(uint64_t) * NA_MAX_S * KMAX);
+constexpr size_t O_ITEMS = O_T + al(sizeof(uint64_t) * NA_MAX_S * NA_KMAX);
 constexpr size_t O_PREFIX = O_ITEMS + al(sizeof(Item) * NA_MAX_S * NA_MAX_ITEMS_PER_SERIES);
-constexpr size_t O_LEVEL = O_PREFIX + al(sizeof(uint32_t) * NA_MAX_S * KMAX);
-constexpr size_t O_RANK = O_LEVEL + al(sizeof(uint8_t) * NA_MAX_S * KMAX);
-constexpr size_t O_BELOW = O_RANK + al(sizeof(uint64_t) * NA_MAX_S * KMAX);
-constexpr size_t O_TSUB = O_BELOW + al(sizeof(uint64_t) * NA_MAX_S * KMAX);
+constexpr size_t O_LEVEL = O_PREFIX + al(sizeof(uint32_t) * NA_MAX_S * NA_KMAX);
+constexpr size_t O_RANK = O_LEVEL + al(sizeof(uint8_t) * NA_MAX_S * NA_KMAX);
+constexpr size_t O_BELOW = O_RANK + al(sizeof(uint64_t) * NA_MAX_S * NA_KMAX);
+constexpr size_t O_TSUB = O_BELOW + al(sizeof(uint64_t) * NA_MAX_S * NA_KMAX);
 constexpr size_t O_TMID = O_TSUB + al((size_t)NA_MAX_S * NCOARSE);
 constexpr size_t O_TFIN1 = O_TMID + al((size_t)NA_MAX_S * NCOARSE);
 constexpr size_t O_TFIN2 = O_TFIN1 + al((size_t)NA_MAX_S * NCOARSE);
-constexpr size_t O_NGROUPS = O_TFIN2 + al((size_t)NA_MAX_S * KMAX * NFINE);
+constexpr size_t O_NGROUPS = O_TFIN2 + al((size_t)NA_MAX_S * NA_KMAX * NFINE);
 constexpr size_t O_RANGE = O_NGROUPS + al(sizeof(int32_t) * 3 * NA_MAX_S);
 constexpr size_t O_REDO = O_RANGE + al(sizeof(uint32_t) * 2 * NA_MAX_S);
 constexpr size_t O_HIST = O_REDO + 256;
@@ -53,7 +55,7 @@ static __device__ __align__(256) unsigned char g_scratch[RQA_NOALLOC_SCRATCH_BYT
 struct NaPlan {
     int S, K;
     SeriesDev sd[NA_MAX_S];
-    uint64_t T[NA_MAX_S][KMAX];
+    uint64_t T[NA_MAX_S][NA_KMAX];
     int chunk[NA_MAX_S];       // bands per work item
     int item_begin[NA_MAX_S + 1];
 };
@@ -137,7 +139,7 @@ extern "C" int rqa_eps_for_rr_noalloc(const rqa_batch *b, const int32_t *rr_num,
         return RQA_ERR_INVALID_ARG;
     if (b->n_series < 1) return RQA_ERR_INVALID_ARG;
     if (b->n_series > NA_MAX_S) return RQA_ERR_CAPACITY;
-    if (K < 1 || K > RQA_K_MAX || rr_den < 2 || b->offsets[0] != 0) return RQA_ERR_INVALID_ARG;
+    if (K < 1 || K > NA_KMAX || rr_den < 2 || b->offsets[0] != 0) return RQA_ERR_INVALID_ARG;
     for (int k = 0; k < K; ++k)
         if (rr_num[k] < 1 || rr_num[k] >= rr_den || (k && rr_num[k] <= rr_num[k - 1]))
             return RQA_ERR_INVALID_ARG;
@@ -209,6 +211,7 @@ extern "C" int rqa_eps_for_rr_noalloc(const rqa_batch *b, const int32_t *rr_num,
     sb.tab_mid = reinterpret_cast<int8_t *>(scr + O_TMID);
     sb.tab_fin1 = reinterpret_cast<int8_t *>(scr + O_TFIN1);
     sb.tab_fin2 = reinterpret_cast<int8_t *>(scr + O_TFIN2);
+    sb.fin2_stride = (int64_t)NA_KMAX * NFINE;
     int32_t *ng = reinterpret_cast<int32_t *>(scr + O_NGROUPS);
     sb.n_sub = ng;
     sb.n_mid = ng + pl.S;
@@ -224,6 +227,8 @@ extern "C" int rqa_eps_for_rr_noalloc(const rqa_batch *b, const int32_t *rr_num,
     a.items = reinterpret_cast<const Item *>(scr + O_ITEMS);
     a.n_items = n_items;
     a.band = BAND;
+    a.g0 = 0;
+    a.gn = MID_GROUPS;  // K <= NA_KMAX < MID_GROUPS: one middle-round launch
     a.status = status;
     const int grid = (int)(n_items < dv.sm_count * 2 ? n_items : dv.sm_count * 2);
     const int rounds[3] = {R_COARSE, R_MID, R_FINAL};

@@ -9,7 +9,9 @@ namespace rqa {
 // the values and use only bits 30..0.  Exact selection splits a key into an
 // 11-bit coarse digit (bits 30..20), a 10-bit middle digit (19..10) and a
 // 10-bit low digit (9..0).
-constexpr int KMAX = 31;
+constexpr int KMAX = 127;        // targets per series and call
+constexpr int LINE_KMAX = 31;    // targets per line-pass launch (lanes of a warp, 5-bit ranks)
+constexpr int MID_GROUPS = 48;   // middle-round groups per launch (4 KB of shared bins each)
 constexpr int COARSE_SHIFT = 20;
 constexpr int NCOARSE = 1 << 11;   // 2048 coarse buckets
 constexpr int NFINE = 1 << 10;     // 1024 bins per middle / low digit group
@@ -55,7 +57,8 @@ struct SelBufs {
     int8_t *tab_sub;       // [s][NCOARSE] bracket split buckets -> group, -1
     int8_t *tab_mid;       // [s][NCOARSE] coarse bucket -> middle group, -1
     int8_t *tab_fin1;      // [s][NCOARSE] coarse bucket -> final super group, -1
-    int8_t *tab_fin2;      // [s][KMAX][NFINE] (super group, middle digit) -> group
+    int8_t *tab_fin2;      // [s][fin2_stride] = [s][targets][NFINE] (super group, middle digit) -> group
+    int64_t fin2_stride;   // entries of tab_fin2 per series (>= K * NFINE)
     uint32_t *tab_hash;    // [s][NHASH] prefix | group << 21 at slot (prefix * mul) >> 20,
                            // 0x1fffff empty; may be null (two-level tables only)
     uint32_t *hash_mul;    // [s]: the slot multiplier, 0 = no collision-free one (or no table)
@@ -73,6 +76,7 @@ struct CellArgs {
     const Item *items;
     int32_t n_items;
     int32_t band;
+    int32_t g0, gn;          // middle round: the groups [g0, g0 + gn) this launch counts
     // warp-level work (line pass): units of `chunk` consecutive bands of the
     // series order[0..n_pos)
     const int32_t *order;    // series, largest first
@@ -95,12 +99,14 @@ cudaError_t launch_select(int round, const SelBufs &sb, const SeriesDev *series,
                           uint64_t *lt_out, int *status, cudaStream_t st);
 
 struct LineBufs {
-    const float *eps;      // [s*K + k], ascending per series
-    uint64_t *count;       // [s*K + k]
-    uint32_t *lmax;        // [s*K + k]
-    uint64_t *hshort;      // [s][K][LSH]: P_k(l) for l = 1..LSH
+    const float *eps;      // [s*kstride + k], ascending per series
+    uint64_t *count;       // [s*kstride + k]
+    uint32_t *lmax;        // [s*kstride + k]
+    uint64_t *hshort;      // [s][kstride][LSH]: P_k(l) for l = 1..LSH
     uint64_t *hist;        // caller's full histogram or nullptr
     const int64_t *hist_off;  // device [S+1] offsets into hist (nullptr if no hist)
+    int32_t k0;            // line pass: first target of this launch's group
+    int32_t kstride;       // targets per series in all arrays above (the call's K)
 };
 cudaError_t launch_lines(const CellArgs &a, const LineBufs &lb, int K, int grid, int embed,
                          cudaStream_t st);

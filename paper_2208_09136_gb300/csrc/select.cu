@@ -44,7 +44,7 @@ int count_smem_bytes(int round, int K)
     switch (round) {
     case R_COARSE: return NCOARSE * 4;
     case R_COARSE_SUB: return (NCOARSE + NSUB_MAX * NFINE) * 4 + NCOARSE;
-    case R_MID: return K * NFINE * 4 + NCOARSE;
+    case R_MID: return (K < MID_GROUPS ? K : MID_GROUPS) * NFINE * 4 + NCOARSE;
     default: {  // tables only (final-round keys are rare): the hash or the two levels
         const int two = NCOARSE + 1 + K * NFINE;
         return two > NHASH * 4 ? two : NHASH * 4;
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
     __shared__ unsigned long long below_sh;
     const int nbins_max = (ROUND == R_COARSE) ? NCOARSE
                         : (ROUND == R_COARSE_SUB) ? NCOARSE + NSUB_MAX * NFINE
-                        : (ROUND == R_MID) ? K * NFINE : 0;
+                        : (ROUND == R_MID) ? (K < MID_GROUPS ? K : MID_GROUPS) * NFINE : 0;
     uint32_t *h = reinterpret_cast<uint32_t *>(smem);
     int8_t *t1 = reinterpret_cast<int8_t *>(h + nbins_max);
     int8_t *t2 = t1 + NCOARSE;
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
             int nb;
             if (ROUND == R_COARSE) nb = sb.redo[item.s] ? NCOARSE : 0;
             else if (ROUND == R_COARSE_SUB) nb = sb.n_sub[item.s] ? NCOARSE + sb.n_sub[item.s] * NFINE : 0;
-            else if (ROUND == R_MID) nb = sb.n_mid[item.s] * NFINE;
+            else if (ROUND == R_MID) nb = max(0, min(sb.n_mid[item.s] - a.g0, a.gn)) * NFINE;
             else nb = sb.n_fin[item.s] * NFINE;
             nb_used_sh = nb;
             next_band = item.b_lo;
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
             src += (int64_t)item.s * NCOARSE;
             for (int x = threadIdx.x; x < NCOARSE; x += NT) t1[x] = src[x];
             if (ROUND == R_FINAL) {
-                const int8_t *s2 = sb.tab_fin2 + (int64_t)item.s * KMAX * NFINE;
+                const int8_t *s2 = sb.tab_fin2 + (int64_t)item.s * sb.fin2_stride;
                 for (int x = threadIdx.x; x < K * NFINE; x += NT) t2[1 + x] = s2[x];
                 if (threadIdx.x == 0) t2[0] = -1;
             }
@@ -205,8 +205,10 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
                         const int bin = g < 0 ? c : NCOARSE + g * NFINE + fine;
                         red_shared_if(&h[bin], valid && key - klo <= kspan);
                     } else if (ROUND == R_MID) {
-                        const int g = t1[c];
-                        red_shared_if(&h[max(g, 0) * NFINE + fine], valid && g >= 0);
+                        // groups outside this launch's window [g0, g0 + gn) wait for another
+                        const uint32_t gw = (uint32_t)((int)t1[c] - a.g0);
+                        red_shared_if(&h[min(gw, (uint32_t)(nbins_max / NFINE - 1)) * NFINE + fine],
+                                      valid && gw < (uint32_t)a.gn);
                     } else if (FAST) {
                         // one probe: the slot holds the only target prefix
                         // that can map there.  Empty slots hold group 0 with
@@ -256,7 +258,8 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
             atomicAdd(reinterpret_cast<unsigned long long *>(sb.hist + (int64_t)item.s * sb.hstride + cb),
                       below_sh);
         }
-        uint64_t *gh = sb.hist + (int64_t)item.s * sb.hstride + (ROUND >= R_MID ? NCOARSE : 0);
+        uint64_t *gh = sb.hist + (int64_t)item.s * sb.hstride + (ROUND >= R_MID ? NCOARSE : 0) +
+                       (ROUND == R_MID ? (int64_t)a.g0 * NFINE : 0);
         for (int x = threadIdx.x; x < (GLOBAL_BINS ? 0 : nb_used); x += NT) {
             const uint32_t v = h[x];
             if (v) {
@@ -296,6 +299,7 @@ cudaError_t launch_count(int round, const CellArgs &a, const SelBufs &sb, int K,
     if (!a.y || !a.series || !a.items || !a.queue || !a.status || !sb.hist || K < 1 || K > KMAX ||
         grid < 1 || a.n_items < 1 || a.band != BAND)
         return cudaErrorInvalidValue;
+    if (round == R_MID && (a.g0 < 0 || a.gn < 1 || a.gn > MID_GROUPS)) return cudaErrorInvalidValue;
     switch (round) {
     case R_COARSE: return launch_count_m<R_COARSE>(a, sb, K, grid, embed, st);
     case R_COARSE_SUB: return launch_count_m<R_COARSE_SUB>(a, sb, K, grid, embed, st);
@@ -519,7 +523,7 @@ k_select(SelBufs sb, const SeriesDev *series, int s_begin, int K, float *eps_out
         }
         // final-round tables for all targets (every target is at level 2 now)
         int8_t *f1 = sb.tab_fin1 + (int64_t)s * NCOARSE;
-        int8_t *f2 = sb.tab_fin2 + (int64_t)s * KMAX * NFINE;
+        int8_t *f2 = sb.tab_fin2 + (int64_t)s * sb.fin2_stride;
         uint32_t *fh = sb.tab_hash ? sb.tab_hash + (int64_t)s * NHASH : nullptr;
         for (int x = t; x < NCOARSE; x += THREADS) f1[x] = -1;
         for (int x = t; x < K * NFINE; x += THREADS) f2[x] = -1;
@@ -574,7 +578,7 @@ k_select(SelBufs sb, const SeriesDev *series, int s_begin, int K, float *eps_out
     // R_FINAL: the low digit completes the key
     {
         const int8_t *f1 = sb.tab_fin1 + (int64_t)s * NCOARSE;
-        const int8_t *f2 = sb.tab_fin2 + (int64_t)s * KMAX * NFINE;
+        const int8_t *f2 = sb.tab_fin2 + (int64_t)s * sb.fin2_stride;
         if (t < K) {
             const int g1 = f1[pre[t] >> 10];
             grp[t] = (g1 < 0) ? -1 : f2[g1 * NFINE + (pre[t] & (NFINE - 1))];

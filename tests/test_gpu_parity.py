@@ -159,11 +159,49 @@ def test_device_errors_reported(rqa_lib):
     assert rqa.rqa_status(ctx) == 3
     assert rqa.rqa_status(ctx) == 0  # cleared after reading
     # host-side validation
-    for bad in ([0], [5, 5], [100], list(range(1, 33))):
-        with pytest.raises(rqa.RqaError):
-            rqa.eps_for_rr(ctx, batch, bad, 100)
+    for bad, den in (([0], 100), ([5, 5], 100), ([100], 100), (list(range(1, 129)), 1000)):
+        with pytest.raises(rqa.RqaError):  # zero, repeated, = den, K > RQA_K_MAX
+            rqa.eps_for_rr(ctx, batch, bad, den)
     short = rqa.Batch.from_numpy([y[:4]], 3, 2)  # Ne = 0
     with pytest.raises(rqa.RqaError) as ei:
         rqa.eps_for_rr(ctx, short, [1, 2], 100)
     assert ei.value.code == 2
     ctx.close()
+
+
+@pytest.mark.parametrize("schedule", SCHEDS)
+def test_rr_up_to_99(rqa_lib, schedule):
+    """RR = 1..99 % (Sect. 2 averages up to RR* = 99): 99 targets per call,
+    middle round in windows of 48 groups and the line pass in four sweeps of
+    at most 31 targets; bit-exact against the oracle."""
+    rng = np.random.default_rng(99)
+    ys = [rng.standard_normal(300).astype(np.float32),
+          (np.sin(2 * np.pi * np.arange(1500) / 20.3) + 0.3 * rng.standard_normal(1500)).astype(np.float32),
+          (np.arange(120) % 9).astype(np.float32)]
+    rr = list(range(1, 100))
+    g = gpu_run(ys, 3, 2, rr, 100, lmin=(2, 3, 5), schedule=schedule)
+    for s, y in enumerate(ys):
+        ref = oracle_series(y, 3, 2, rr, 100, lmin=(2, 3, 5))
+        assert_series_equal(g, s, ref, "RR 1..99")
+
+
+@pytest.mark.parametrize("K", [31, 32, 62, 63, 127])
+def test_target_count_group_boundaries(rqa_lib, K):
+    """K around the 31-target line-pass groups and the 48-group middle-round
+    windows, up to K = RQA_K_MAX = 127 (rr_den = 128)."""
+    rng = np.random.default_rng(K)
+    ys = [rng.standard_normal(400).astype(np.float32), rng.standard_normal(77).astype(np.float32)]
+    rr = list(range(1, K + 1))
+    g = gpu_run(ys, 2, 1, rr, 128, lmin=(2, 4))
+    for s, y in enumerate(ys):
+        ref = oracle_series(y, 2, 1, rr, 128, lmin=(2, 4))
+        assert_series_equal(g, s, ref, f"K={K}")
+
+
+def test_noalloc_rejects_more_than_31_targets(rqa_lib):
+    import torch
+    rqa = rqa_lib
+    batch = rqa.Batch.from_numpy([np.ones(50, np.float32)], 1, 1)
+    eps = torch.empty(32, dtype=torch.float32, device="cuda")
+    with pytest.raises(rqa.RqaError):
+        rqa.rqa_eps_for_rr_noalloc(batch, list(range(1, 33)), 100, eps)
