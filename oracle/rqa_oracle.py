@@ -58,6 +58,23 @@ def target_counts(p: int, rr_num: Sequence[int], rr_den: int) -> np.ndarray:
     return np.array(out, dtype=np.uint64)
 
 
+def target_counts_loi(ne: int, rr_num: Sequence[int], rr_den: int) -> np.ndarray:
+    """Upper-triangle targets when RR counts the whole Ne x Ne matrix with the
+    line of identity, as Eq. 3 is written: a rate needs 2 C + Ne >=
+    ceil(rr_num Ne^2 / rr_den) recurrent cells (C upper-triangle cells, both
+    triangles alike, Ne diagonal cells always recurrent), so
+    T_k = ceil((ceil(rr_num Ne^2 / rr_den) - Ne) / 2).  A rate the line of
+    identity reaches by itself (T_k <= 0) has no threshold: ValueError."""
+    out = []
+    for r in rr_num:
+        full = -((-int(r) * int(ne) * int(ne)) // int(rr_den))
+        t = -((-(full - int(ne))) // 2)
+        if t <= 0:
+            raise ValueError("the line of identity alone reaches this recurrence rate")
+        out.append(t)
+    return np.array(out, dtype=np.uint64)
+
+
 def diagonal_distances(y: np.ndarray, m: int, tau: int, delta: int) -> np.ndarray:
     """d(i, i+delta) for i = 0 .. Ne-delta-1, maximum norm in FP32 (Eq. 1)."""
     y = np.asarray(y, dtype=np.float32)
@@ -78,16 +95,19 @@ def all_distances(y: np.ndarray, m: int, tau: int) -> np.ndarray:
 
 
 def eps_for_rr(y: np.ndarray, m: int, tau: int, rr_num: Sequence[int], rr_den: int,
-               dist: np.ndarray = None) -> Dict[str, np.ndarray]:
+               dist: np.ndarray = None, loi: bool = False) -> Dict[str, np.ndarray]:
     """Exact thresholds by sorting all distances (Sect. 2: RR fixed first, eps from it).
 
-    Returns eps (FP32), T, count_le = #{d <= eps}, count_lt = #{d < eps}.
+    Returns eps (FP32), T, count_le = #{d <= eps}, count_lt = #{d < eps} (upper
+    triangle).  loi: RR over the whole matrix with the line of identity
+    (target_counts_loi) instead of over the upper triangle.
     """
     d = all_distances(y, m, tau) if dist is None else dist
     p = d.shape[0]
     if p == 0:
         raise ValueError("fewer than two embedded vectors")
-    t = target_counts(p, rr_num, rr_den)
+    ne = embedded_count(len(y), m, tau)
+    t = target_counts_loi(ne, rr_num, rr_den) if loi else target_counts(p, rr_num, rr_den)
     s = np.sort(d, kind="stable")
     eps = s[(t - 1).astype(np.int64)].astype(np.float32)
     le = np.searchsorted(s, eps, side="right").astype(np.uint64)
@@ -145,19 +165,28 @@ def line_hist(y: np.ndarray, m: int, tau: int, eps: Sequence[float]) -> Dict[str
     return {"hist": hist, "count": count, "stencil": stencil, "lmax": lmax}
 
 
-def det_from_hist(hist: np.ndarray, count: np.ndarray, lmin: Sequence[int]) -> np.ndarray:
+def det_from_hist(hist: np.ndarray, count: np.ndarray, lmin: Sequence[int],
+                  loi: bool = False) -> np.ndarray:
     """DET_k(lmin) = sum_{l >= lmin} l P_k(l) / C_k in FP64 (Eq. 4).
 
-    Returns an array of shape (K, len(lmin)).
+    loi: over the whole matrix with the line of identity, as Eq. 4 is written:
+    every upper-triangle line twice plus the identity line of length Ne =
+    hist.shape[1] + 1, i.e. (2 sum_{l >= lmin} l P_k(l) + Ne [Ne >= lmin]) /
+    (2 C_k + Ne).  Returns an array of shape (K, len(lmin)).
     """
     k, lmax_len = hist.shape
+    ne = lmax_len + 1
     out = np.zeros((k, len(lmin)), dtype=np.float64)
     lengths = np.arange(1, lmax_len + 1, dtype=object)
     for kk in range(k):
         row = [int(v) for v in hist[kk]]
         for j, lm in enumerate(lmin):
             num = sum(int(l) * c for l, c in zip(lengths, row) if l >= lm)
-            out[kk, j] = float(num) / float(int(count[kk]))
+            den = int(count[kk])
+            if loi:
+                num = 2 * num + (ne if ne >= lm else 0)
+                den = 2 * den + ne
+            out[kk, j] = float(num) / float(den)
     return out
 
 
@@ -170,7 +199,7 @@ def det_avg(det: np.ndarray) -> np.ndarray:
     return acc / np.float64(k)
 
 
-def line_measures(hist: np.ndarray, lmin: Sequence[int]) -> Dict[str, np.ndarray]:
+def line_measures(hist: np.ndarray, lmin: Sequence[int], loi: bool = False) -> Dict[str, np.ndarray]:
     """Average diagonal line length L and line-length entropy ENTR (K, len(lmin)).
 
     Sect. 2 closes by noting that the averaging over RR applies to other RQA
@@ -183,12 +212,16 @@ def line_measures(hist: np.ndarray, lmin: Sequence[int]) -> Dict[str, np.ndarray
                                                       NaN when N_l = 0)
         ENTR = -sum_{l >= lmin} p(l) ln p(l),  p(l) = P(l) / N_l
                (natural logarithm, FP64, summed over l ascending; 0 when N_l = 0).
+    loi: the whole matrix with the line of identity (P(l) -> 2 P(l), plus one
+    line of length Ne = hist.shape[1] + 1), as for det_from_hist.
     """
     k, nl = hist.shape
     L = np.zeros((k, len(lmin)), dtype=np.float64)
     E = np.zeros((k, len(lmin)), dtype=np.float64)
     for kk in range(k):
         row = [int(v) for v in hist[kk]]
+        if loi:  # whole matrix: each line twice, plus the identity line of length Ne
+            row = [2 * c for c in row] + [1]
         for j, lm in enumerate(lmin):
             n_lines = sum(c for l, c in enumerate(row, start=1) if l >= lm)
             mass = sum(l * c for l, c in enumerate(row, start=1) if l >= lm)
@@ -209,11 +242,11 @@ def measure_avg(v: np.ndarray) -> np.ndarray:
 
 
 def rqa_det_avg(y: np.ndarray, m: int, tau: int, rr_num: Sequence[int], rr_den: int,
-                lmin: Sequence[int] = (2,)) -> Dict[str, np.ndarray]:
+                lmin: Sequence[int] = (2,), loi: bool = False) -> Dict[str, np.ndarray]:
     """The whole hot path on one series: eps_k, line statistics, DET_k, mean."""
-    sel = eps_for_rr(y, m, tau, rr_num, rr_den)
+    sel = eps_for_rr(y, m, tau, rr_num, rr_den, loi=loi)
     lines = line_hist(y, m, tau, sel["eps"])
-    det = det_from_hist(lines["hist"], lines["count"], lmin)
+    det = det_from_hist(lines["hist"], lines["count"], lmin, loi=loi)
     out = dict(sel)
     out.update(lines)
     out["det"] = det

@@ -349,3 +349,72 @@ def test_line_measures_full_matrix_brute_force(seed, n, m, tau):
             E2 = -sum((h2[l] / nl) * math.log(h2[l] / nl) for l in range(lm, len(h2)) if h2[l])
             assert r["L"][k, j] == pytest.approx(L2, rel=1e-15)
             assert r["entr"][k, j] == pytest.approx(E2, rel=1e-13, abs=1e-15)
+
+
+# ------------------------------------------------- line of identity (Eq. 3-4 as written)
+def _brute_full_loi(y, m, tau, rr_num, rr_den, lmin):
+    """Eq. 3 and Eq. 4 over the whole Ne x Ne matrix, main diagonal included,
+    by pure-Python counting and run scanning of every diagonal."""
+    n = len(y)
+    ne = n - (m - 1) * tau
+    D = [[_d32(y, i, j, m, tau) if i != j else np.float32(0.0) for j in range(ne)] for i in range(ne)]
+    vals = sorted({D[i][j] for i in range(ne) for j in range(ne) if i != j})
+    out = []
+    for num in rr_num:
+        need = -((-num * ne * ne) // rr_den)
+        eps = next(v for v in vals if sum(1 for i in range(ne) for j in range(ne) if D[i][j] <= v) >= need)
+        rec = [[D[i][j] <= eps for j in range(ne)] for i in range(ne)]
+        cfull = sum(rec[i][j] for i in range(ne) for j in range(ne))
+        hist = [0] * (ne + 1)
+        for off in range(-(ne - 1), ne):
+            run = 0
+            cells = [(i, i + off) for i in range(ne) if 0 <= i + off < ne]
+            for cell in cells + [None]:
+                if cell is not None and rec[cell[0]][cell[1]]:
+                    run += 1
+                else:
+                    if run:
+                        hist[run] += 1
+                    run = 0
+        det = [sum(l * hist[l] for l in range(lm, ne + 1)) / cfull for lm in lmin]
+        nls = [sum(hist[l] for l in range(lm, ne + 1)) for lm in lmin]
+        L = [sum(l * hist[l] for l in range(lm, ne + 1)) / nl for lm, nl in zip(lmin, nls)]
+        E = [-sum((hist[l] / nl) * math.log(hist[l] / nl) for l in range(lm, ne + 1) if hist[l])
+             for lm, nl in zip(lmin, nls)]
+        out.append(dict(eps=eps, cfull=cfull, det=det, L=L, E=E))
+    return out
+
+
+@pytest.mark.parametrize("seed,n,m,tau", [(0, 14, 1, 1), (1, 19, 2, 1), (2, 24, 3, 2)])
+def test_loi_reading_equals_full_matrix_brute_force(seed, n, m, tau):
+    """With the line of identity counted (Eq. 3-4 as printed): eps, the full
+    recurrence count 2C + Ne, DET, L and ENTR against the whole matrix."""
+    rng = np.random.default_rng(seed)
+    y = (rng.integers(0, 5, size=n) * 0.5).astype(np.float32) if seed % 2 else \
+        rng.standard_normal(n).astype(np.float32)
+    ne = n - (m - 1) * tau
+    rr_num = [r for r in (10, 20, 35, 50, 80) if -((-r * ne * ne) // 100) > ne]
+    lmin = (1, 2, 3)
+    orc = O.rqa_det_avg(y, m, tau, rr_num, 100, lmin, loi=True)
+    meas = O.line_measures(orc["hist"], lmin, loi=True)
+    for k, b in enumerate(_brute_full_loi(y, m, tau, rr_num, 100, lmin)):
+        assert orc["eps"][k] == b["eps"]
+        assert 2 * int(orc["count_le"][k]) + ne == b["cfull"]
+        for j in range(len(lmin)):
+            assert orc["det"][k, j] == pytest.approx(b["det"][j], rel=1e-15)
+            assert meas["L"][k, j] == pytest.approx(b["L"][j], rel=1e-15)
+            assert meas["entr"][k, j] == pytest.approx(b["E"][j], rel=1e-13, abs=1e-15)
+
+
+def test_loi_constant_series_and_rejection():
+    """Constant series: every cell recurrent at eps = 0, so DET(1) = 1 exactly
+    and DET(2) = 1 - 2 / Ne^2 (only the two corner cells are single points);
+    a rate that the identity line alone reaches has no threshold."""
+    ne = 50
+    r = O.rqa_det_avg(np.full(ne, 3.0, np.float32), 1, 1, [5, 60], 100, (1, 2), loi=True)
+    assert np.all(r["eps"] == 0.0)
+    assert np.all(r["det"][:, 0] == 1.0)
+    assert np.all(r["det"][:, 1] == (ne * ne - 2) / (ne * ne))
+    with pytest.raises(ValueError):
+        O.target_counts_loi(50, [2], 100)  # ceil(0.02 * 2500) = 50 <= Ne
+    assert list(O.target_counts_loi(50, [3], 100)) == [13]  # ceil((75 - 50) / 2)
