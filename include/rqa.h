@@ -103,6 +103,18 @@ typedef struct {
  * default stream.  This flag turns that off. */
 #define RQA_FLAG_NO_GRAPHS 1
 
+/* Count the line of identity, as Eq. 3 and Eq. 4 are printed: RR over the
+ * whole Ne x Ne matrix (both triangles and the Ne always-recurrent diagonal
+ * cells), so a target needs 2 C + Ne >= ceil(rr_num Ne^2 / rr_den) and the
+ * upper-triangle target is T_k = ceil((ceil(rr_num Ne^2 / rr_den) - Ne) / 2);
+ * DET_k(lmin) = (2 sum_{l>=lmin} l P_k(l) + Ne [Ne >= lmin]) / (2 C_k + Ne),
+ * and rqa_line_measures adds the identity line (length Ne) to twice the
+ * upper-triangle histogram.  A target that the identity line reaches alone
+ * (T_k <= 0) is RQA_ERR_INVALID_ARG.  Counts, histograms and L_max stay those
+ * of the upper triangle.  Without the flag the line of identity is left out
+ * everywhere (counts over the P = Ne(Ne-1)/2 pairs i < j). */
+#define RQA_FLAG_LOI 2
+
 /* A batch of S series stored back to back in one device buffer. */
 typedef struct {
     const float *y;          /* device, offsets[S] FP32 values, caller-owned */

@@ -21,7 +21,7 @@ from .abi import (  # noqa: F401
     rqa_sketch, rqa_mlp_forward, rqa_mlp_backward, rqa_adam_step, rqa_set_bracket_model,
     rqa_bracket_stats, RQA_MLP_PARAMS, RQA_MLP_ACTS, RQA_MLP_OUT,
     rqa_eps_for_rr_noalloc, RQA_NOALLOC_MAX_SERIES,
-    rqa_graph_replays, rqa_autotune, RQA_FLAG_NO_GRAPHS, rqa_line_measures,
+    rqa_graph_replays, rqa_autotune, RQA_FLAG_NO_GRAPHS, RQA_FLAG_LOI, rqa_line_measures,
     RQA_SCHED_BATCHED, RQA_SCHED_PER_SERIES, RQA_SELECT_AUTO, RQA_SELECT_BRACKET,
     RQA_SELECT_RADIX, RQA_K_MAX, RQA_LMIN_MAX, RQA_FEATURES,
 )

@@ -45,6 +45,7 @@ class _Config(ctypes.Structure):
 
 
 RQA_FLAG_NO_GRAPHS = 1
+RQA_FLAG_LOI = 2
 
 
 class _Batch(ctypes.Structure):

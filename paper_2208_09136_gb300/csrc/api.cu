@@ -55,6 +55,7 @@ struct rqa_ctx {
     int band = 16;          // diagonals per band of the counting rounds
     int band_lines = 0;     // ... of the line pass (0 = tuned default)
     bool band_fixed = false;  // the caller chose the band: rqa_autotune keeps it
+    bool loi = false;         // RQA_FLAG_LOI: rates and DET over the whole matrix
     int bpsm = 0;
     int sm_count = 0;
 
@@ -249,9 +250,21 @@ int make_plan(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_
     }
     if (rr_num) {
         pl.T.resize((size_t)S * K);
-        for (int s = 0; s < S; ++s)
-            if (rqa_target_counts(pl.sd[s].P, rr_num, rr_den, K, &pl.T[(size_t)s * K]) != RQA_OK)
+        for (int s = 0; s < S; ++s) {
+            uint64_t *T = &pl.T[(size_t)s * K];
+            if (rqa_target_counts(pl.sd[s].P, rr_num, rr_den, K, T) != RQA_OK)
                 return RQA_ERR_INVALID_ARG;
+            if (c->loi) {  // whole matrix: 2 C + Ne >= ceil(rr Ne^2 / den)
+                const unsigned __int128 ne = (unsigned __int128)(uint64_t)pl.sd[s].ne;
+                for (int k = 0; k < K; ++k) {
+                    const unsigned __int128 full =
+                        ((unsigned __int128)(uint64_t)rr_num[k] * ne * ne + (unsigned)(rr_den - 1)) /
+                        (unsigned)rr_den;
+                    if (full <= ne) return RQA_ERR_INVALID_ARG;  // the identity line alone reaches it
+                    T[k] = (uint64_t)((full - ne + 1) / 2);
+                }
+            }
+        }
     }
     // CTA work items (counting rounds): runs of consecutive bands of one
     // series, about three per persistent CTA and at least four bands per warp,
@@ -719,7 +732,7 @@ int rqa_create(rqa_ctx **out, const rqa_config *cfg)
     if (!cfg) cfg = &def;
     for (int i = 0; i < 3; ++i)
         if (cfg->reserved[i]) return RQA_ERR_INVALID_ARG;
-    if (cfg->flags & ~RQA_FLAG_NO_GRAPHS) return RQA_ERR_INVALID_ARG;
+    if (cfg->flags & ~(RQA_FLAG_NO_GRAPHS | RQA_FLAG_LOI)) return RQA_ERR_INVALID_ARG;
     if (cfg->schedule != RQA_SCHED_BATCHED && cfg->schedule != RQA_SCHED_PER_SERIES)
         return RQA_ERR_INVALID_ARG;
     if (cfg->select < RQA_SELECT_AUTO || cfg->select > RQA_SELECT_BRACKET) return RQA_ERR_INVALID_ARG;
@@ -742,6 +755,7 @@ int rqa_create(rqa_ctx **out, const rqa_config *cfg)
     c->band_lines = cfg->band;
     c->band_fixed = cfg->band != 0;
     c->graphs = !(cfg->flags & RQA_FLAG_NO_GRAPHS);
+    c->loi = (cfg->flags & RQA_FLAG_LOI) != 0;
     c->bpsm = cfg->blocks_per_sm;
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess ||
@@ -859,6 +873,7 @@ int rqa_det_avg(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t r
         auto ptr = [&](const void *p) { put((uint64_t)(uintptr_t)p); };
         put((uint64_t)pl.S); put((uint64_t)K); put((uint64_t)n_lmin); put((uint64_t)rr_den);
         put(bracket); put((uint64_t)c->schedule); put((uint64_t)pl.band_lines); put(c->timing);
+        put(c->loi);
         uint32_t mb;
         std::memcpy(&mb, &c->margin, 4);
         put(mb);
@@ -899,7 +914,7 @@ int rqa_det_avg(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t r
         LineBufs lb;
         if (int rc = lines_and_outputs(c, pl, e, lo, lb)) return rc;
         if (int rc = launched(c, launch_finalize_det(lb, pl.d_sd, pl.S, K, pl.d_lmin, n_lmin, det_out,
-                                                     det_avg, c->stream)))
+                                                     det_avg, c->loi, c->stream)))
             return rc;
         if (int rc = line_outputs_tail(c, pl, lo, lb)) return rc;
         mark(c, 6);
@@ -984,7 +999,7 @@ int rqa_line_measures(rqa_ctx *c, const rqa_batch *b, int32_t K, const uint64_t 
     }
     if (int rc = upload_plan(c, pl, lmin, n_lmin, hist_offsets)) return rc;
     return launched(c, launch_line_measures(hist, pl.d_hoff, pl.S, K, pl.d_lmin, n_lmin, L, E, L_avg,
-                                            entr_avg, c->stream));
+                                            entr_avg, c->loi, c->stream));
 }
 
 int rqa_set_timing(rqa_ctx *c, int enable)

@@ -7,9 +7,10 @@
 namespace rqa {
 
 // DET_k(lmin) = (C_k - sum_{l < lmin} l P_k(l)) / C_k  (Eq. 4), an FP64 ratio of
-// exact integers, and the average over k in order (Eq. avgDET).
-__global__ void k_finalize_det(LineBufs lb, int K, const int32_t *lmin, int n_lmin, double *det,
-                               double *det_avg)
+// exact integers, and the average over k in order (Eq. avgDET).  loi: the
+// whole matrix with the line of identity, (2 num + Ne [Ne >= lmin]) / (2 C + Ne).
+__global__ void k_finalize_det(LineBufs lb, const SeriesDev *series, int K, const int32_t *lmin,
+                               int n_lmin, double *det, double *det_avg, bool loi)
 {
     __shared__ double dk[KMAX * LMIN_MAX];
     const int s = blockIdx.x;
@@ -21,7 +22,13 @@ __global__ void k_finalize_det(LineBufs lb, int K, const int32_t *lmin, int n_lm
         for (int j = 0; j < n_lmin; ++j) {
             uint64_t shortmass = 0;
             for (int l = 1; l < lmin[j]; ++l) shortmass += (uint64_t)l * h[l - 1];
-            const double v = (double)(C - shortmass) / (double)C;
+            uint64_t num = C - shortmass, den = C;
+            if (loi) {
+                const uint64_t ne = (uint64_t)series[s].ne;
+                num = 2 * num + (ne >= (uint64_t)lmin[j] ? ne : 0);
+                den = 2 * den + ne;
+            }
+            const double v = (double)num / (double)den;
             dk[t * LMIN_MAX + j] = v;
             if (det) det[o * n_lmin + j] = v;
         }
@@ -34,12 +41,12 @@ __global__ void k_finalize_det(LineBufs lb, int K, const int32_t *lmin, int n_lm
     }
 }
 
-cudaError_t launch_finalize_det(const LineBufs &lb, const SeriesDev *, int S, int K,
+cudaError_t launch_finalize_det(const LineBufs &lb, const SeriesDev *series, int S, int K,
                                 const int32_t *lmin_dev, int n_lmin, double *det,
-                                double *det_avg, cudaStream_t st)
+                                double *det_avg, bool loi, cudaStream_t st)
 {
     if (K < 1 || K > KMAX) return cudaErrorInvalidValue;
-    k_finalize_det<<<S, 128, 0, st>>>(lb, K, lmin_dev, n_lmin, det, det_avg);  // one thread per target
+    k_finalize_det<<<S, 128, 0, st>>>(lb, series, K, lmin_dev, n_lmin, det, det_avg, loi);  // a thread per target
     return cudaGetLastError();
 }
 

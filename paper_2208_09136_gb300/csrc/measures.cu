@@ -7,6 +7,8 @@
 //   ENTR = -sum_{l >= lmin} p(l) ln p(l),  p(l) = P(l) / N_l.
 // The input is the full histogram the line pass wrote (upper triangle; both
 // triangles hold the same lines, so the ratios equal the full-matrix ones).
+// loi: the whole matrix with the line of identity, i.e. P(l) -> 2 P(l) plus
+// one line of length Ne.
 #include <cstdint>
 #include "rqa_common.cuh"
 
@@ -18,7 +20,7 @@ constexpr int MT = 256;  // threads per (series, target)
 // then the entropy terms in FP64 (a fixed reduction tree).
 __global__ void __launch_bounds__(MT)
 k_line_measures(const uint64_t *__restrict__ hist, const int64_t *__restrict__ hoff, int K,
-                const int32_t *__restrict__ lmin, int n_lmin, double *L_out, double *E_out)
+                const int32_t *__restrict__ lmin, int n_lmin, double *L_out, double *E_out, bool loi)
 {
     __shared__ unsigned long long red_n[MT / 32][LMIN_MAX], red_m[MT / 32][LMIN_MAX];
     __shared__ double red_e[MT / 32][LMIN_MAX];
@@ -27,12 +29,14 @@ k_line_measures(const uint64_t *__restrict__ hist, const int64_t *__restrict__ h
     const int64_t nl = (hoff[s + 1] - hoff[s]) / K;  // lengths 1..nl
     const uint64_t *row = hist + hoff[s] + (int64_t)k * nl;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    const unsigned long long mult = loi ? 2ull : 1ull;  // lines per upper-triangle line
+    const int64_t ne = nl + 1;                           // the identity line's length
 
     unsigned long long n[LMIN_MAX], m[LMIN_MAX];
 #pragma unroll
     for (int j = 0; j < LMIN_MAX; ++j) n[j] = m[j] = 0ull;
     for (int64_t l = 1 + t; l <= nl; l += MT) {
-        const unsigned long long c = row[l - 1];
+        const unsigned long long c = mult * row[l - 1];
         if (!c) continue;
 #pragma unroll
         for (int j = 0; j < LMIN_MAX; ++j)
@@ -41,6 +45,13 @@ k_line_measures(const uint64_t *__restrict__ hist, const int64_t *__restrict__ h
                 m[j] += c * (unsigned long long)l;
             }
     }
+    if (loi && t == 0)  // the line of identity: one line of length Ne
+#pragma unroll
+        for (int j = 0; j < LMIN_MAX; ++j)
+            if (j < n_lmin && ne >= lmin[j]) {
+                n[j] += 1ull;
+                m[j] += (unsigned long long)ne;
+            }
 #pragma unroll
     for (int j = 0; j < LMIN_MAX; ++j) {
         for (int o = 16; o > 0; o >>= 1) {
@@ -70,7 +81,7 @@ k_line_measures(const uint64_t *__restrict__ hist, const int64_t *__restrict__ h
 #pragma unroll
     for (int j = 0; j < LMIN_MAX; ++j) e[j] = 0.0;
     for (int64_t l = 1 + t; l <= nl; l += MT) {
-        const unsigned long long c = row[l - 1];
+        const unsigned long long c = mult * row[l - 1];
         if (!c) continue;
 #pragma unroll
         for (int j = 0; j < LMIN_MAX; ++j)
@@ -79,6 +90,13 @@ k_line_measures(const uint64_t *__restrict__ hist, const int64_t *__restrict__ h
                 e[j] -= p * log(p);
             }
     }
+    if (loi && t == 0)
+#pragma unroll
+        for (int j = 0; j < LMIN_MAX; ++j)
+            if (j < n_lmin && ne >= lmin[j]) {
+                const double p = 1.0 / (double)tot_n[j];
+                e[j] -= p * log(p);
+            }
 #pragma unroll
     for (int j = 0; j < LMIN_MAX; ++j) {
         for (int o = 16; o > 0; o >>= 1) e[j] += __shfl_xor_sync(FULL, e[j], o);
@@ -105,12 +123,13 @@ __global__ void k_measure_avg(const double *v, int K, int n_lmin, double *avg)
 
 cudaError_t launch_line_measures(const uint64_t *hist, const int64_t *hoff_dev, int S, int K,
                                  const int32_t *lmin_dev, int n_lmin, double *L_out,
-                                 double *E_out, double *L_avg, double *E_avg, cudaStream_t st)
+                                 double *E_out, double *L_avg, double *E_avg, bool loi,
+                                 cudaStream_t st)
 {
     if (!hist || !hoff_dev || !lmin_dev || S < 1 || K < 1 || K > KMAX || n_lmin < 1 ||
         n_lmin > LMIN_MAX || (L_avg && !L_out) || (E_avg && !E_out))
         return cudaErrorInvalidValue;
-    k_line_measures<<<S * K, MT, 0, st>>>(hist, hoff_dev, K, lmin_dev, n_lmin, L_out, E_out);
+    k_line_measures<<<S * K, MT, 0, st>>>(hist, hoff_dev, K, lmin_dev, n_lmin, L_out, E_out, loi);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (L_avg) k_measure_avg<<<S, 32, 0, st>>>(L_out, K, n_lmin, L_avg);

@@ -113,10 +113,11 @@ cudaError_t launch_lines(const CellArgs &a, const LineBufs &lb, int K, int grid,
 bool lines_band_ok(int embed, int band);
 cudaError_t launch_finalize_det(const LineBufs &lb, const SeriesDev *series, int S, int K,
                                 const int32_t *lmin_dev, int n_lmin, double *det,
-                                double *det_avg, cudaStream_t st);
+                                double *det_avg, bool loi, cudaStream_t st);
 cudaError_t launch_line_measures(const uint64_t *hist, const int64_t *hoff_dev, int S, int K,
                                  const int32_t *lmin_dev, int n_lmin, double *L_out,
-                                 double *E_out, double *L_avg, double *E_avg, cudaStream_t st);
+                                 double *E_out, double *L_avg, double *E_avg, bool loi,
+                                 cudaStream_t st);
 cudaError_t launch_finalize_hist(const LineBufs &lb, const SeriesDev *series, int S, int K,
                                  uint64_t *stencil, cudaStream_t st);
 
