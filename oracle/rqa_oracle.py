@@ -165,6 +165,70 @@ def line_hist(y: np.ndarray, m: int, tau: int, eps: Sequence[float]) -> Dict[str
     return {"hist": hist, "count": count, "stencil": stencil, "lmax": lmax}
 
 
+def column_distances(y: np.ndarray, m: int, tau: int, j: int) -> np.ndarray:
+    """d(i, j) for i = 0 .. Ne-1 (the whole column j, d(j, j) = 0), FP32."""
+    y = np.asarray(y, dtype=np.float32)
+    ne = embedded_count(len(y), m, tau)
+    i = np.arange(ne)
+    d = np.abs(y[i] - y[j])
+    for q in range(1, m):
+        d = np.maximum(d, np.abs(y[i + q * tau] - y[j + q * tau]))
+    return d.astype(np.float32)
+
+
+def vline_hist(y: np.ndarray, m: int, tau: int, eps: Sequence[float],
+               loi: bool = False) -> Dict[str, np.ndarray]:
+    """Vertical line statistics of the whole recurrence matrix per threshold.
+
+    Sect. 2 notes that the averaging applies to other RQA measures; the
+    vertical-line ones (laminarity LAM, trapping time TT; Marwan et al. 2007,
+    Phys. Rep. 438, Sect. 5.1) count maximal runs of recurrent cells along each
+    column j of the Ne x Ne matrix.  The line of identity is left out (the cell
+    (j, j) ends a run) unless loi, where it is recurrent like every d = 0 cell.
+    vhist[k, l-1] = V_k(l) for l = 1 .. Ne-1 (loi: 1 .. Ne, one more column),
+    vmax = longest vertical line.
+    """
+    y = np.asarray(y, dtype=np.float32)
+    eps = np.asarray(eps, dtype=np.float32)
+    k = eps.shape[0]
+    ne = embedded_count(len(y), m, tau)
+    nl = ne if loi else max(ne - 1, 0)
+    vhist = np.zeros((k, nl), dtype=np.uint64)
+    vmax = np.zeros(k, dtype=np.uint32)
+    for j in range(ne):
+        d = column_distances(y, m, tau, j)
+        rec = d[None, :] <= eps[:, None]
+        if not loi:
+            rec[:, j] = False
+        for kk in range(k):
+            runs = _runs(rec[kk])
+            if runs.size:
+                np.add.at(vhist[kk], runs - 1, 1)
+                vmax[kk] = max(int(vmax[kk]), int(runs.max()))
+    return {"vhist": vhist, "vmax": vmax}
+
+
+def lam_tt(vhist: np.ndarray, count: np.ndarray, vmin: Sequence[int], ne: int,
+           loi: bool = False) -> Dict[str, np.ndarray]:
+    """LAM_k(vmin) = sum_{l >= vmin} l V_k(l) / (recurrent cells of the matrix)
+    and TT_k(vmin) = sum_{l >= vmin} l V_k(l) / sum_{l >= vmin} V_k(l), FP64
+    ratios of exact integers.  The recurrent cells are 2 C_k (both triangles,
+    count = upper-triangle C_k), plus Ne with loi.  TT is NaN when no vertical
+    line is vmin long.  Shapes (K, len(vmin))."""
+    k = vhist.shape[0]
+    lam = np.zeros((k, len(vmin)), dtype=np.float64)
+    tt = np.zeros((k, len(vmin)), dtype=np.float64)
+    for kk in range(k):
+        row = [int(v) for v in vhist[kk]]
+        rec = 2 * int(count[kk]) + (ne if loi else 0)
+        for j, vm in enumerate(vmin):
+            mass = sum(l * c for l, c in enumerate(row, start=1) if l >= vm)
+            nv = sum(c for l, c in enumerate(row, start=1) if l >= vm)
+            lam[kk, j] = float(mass) / float(rec)
+            tt[kk, j] = float(mass) / float(nv) if nv else float("nan")
+    return {"lam": lam, "tt": tt}
+
+
 def det_from_hist(hist: np.ndarray, count: np.ndarray, lmin: Sequence[int],
                   loi: bool = False) -> np.ndarray:
     """DET_k(lmin) = sum_{l >= lmin} l P_k(l) / C_k in FP64 (Eq. 4).

@@ -418,3 +418,68 @@ def test_loi_constant_series_and_rejection():
     with pytest.raises(ValueError):
         O.target_counts_loi(50, [2], 100)  # ceil(0.02 * 2500) = 50 <= Ne
     assert list(O.target_counts_loi(50, [3], 100)) == [13]  # ceil((75 - 50) / 2)
+
+
+# ------------------------------------------------------------- vertical lines
+def _brute_vertical(y, m, tau, eps, loi):
+    n = len(y)
+    ne = n - (m - 1) * tau
+    out = []
+    for e in eps:
+        hist = [0] * (ne + 1)
+        for j in range(ne):
+            run = 0
+            for i in list(range(ne)) + [None]:
+                rec = i is not None and (i != j or loi) and _d32(y, i, j, m, tau) <= e if i != j \
+                    else (i is not None and loi)
+                if rec:
+                    run += 1
+                else:
+                    if run:
+                        hist[run] += 1
+                    run = 0
+        out.append(hist)
+    return out
+
+
+@pytest.mark.parametrize("seed,n,m,tau,loi", [(0, 15, 1, 1, False), (1, 21, 2, 1, False),
+                                              (2, 26, 3, 2, True), (3, 18, 2, 3, True)])
+def test_vertical_lines_brute_force(seed, n, m, tau, loi):
+    """V_k(l) by scanning every column of the matrix cell by cell, LAM and TT
+    from it, and the symmetry of the matrix: the vertical lines are the
+    horizontal lines, so the vertical mass equals the recurrence count."""
+    rng = np.random.default_rng(seed)
+    y = (rng.integers(0, 5, size=n) * 0.5).astype(np.float32) if seed % 2 else \
+        rng.standard_normal(n).astype(np.float32)
+    ne = n - (m - 1) * tau
+    rr = [10, 30, 60]
+    sel = O.eps_for_rr(y, m, tau, rr, 100)
+    v = O.vline_hist(y, m, tau, sel["eps"], loi=loi)
+    for k, h in enumerate(_brute_vertical(y, m, tau, sel["eps"], loi)):
+        assert [int(x) for x in v["vhist"][k]] == h[1:1 + v["vhist"].shape[1]]
+        assert int(v["vmax"][k]) == max([l for l in range(len(h)) if h[l]], default=0)
+    mass = (v["vhist"].astype(np.int64) * np.arange(1, v["vhist"].shape[1] + 1)).sum(axis=1)
+    assert np.array_equal(mass, 2 * sel["count_le"].astype(np.int64) + (ne if loi else 0))
+    lt = O.lam_tt(v["vhist"], sel["count_le"], (1, 2), ne, loi=loi)
+    assert np.all(lt["lam"][:, 0] == 1.0)        # every recurrent cell is on a vertical line
+    for k in range(len(rr)):
+        row = [int(x) for x in v["vhist"][k]]
+        n2 = sum(row[1:])
+        m2 = sum(l * c for l, c in enumerate(row, start=1) if l >= 2)
+        assert lt["tt"][k, 1] == m2 / n2 if n2 else math.isnan(lt["tt"][k, 1])
+
+
+def test_vertical_lines_constant_series():
+    """Constant series: column j is recurrent everywhere but at (j, j), so it
+    holds one line of length j and one of length Ne-1-j: V(l) = 2 for every
+    l = 1..Ne-1; with the identity line counted each column is one line of
+    length Ne."""
+    ne = 30
+    y = np.full(ne, 1.5, np.float32)
+    v = O.vline_hist(y, 1, 1, np.array([0.0], np.float32))
+    assert np.all(v["vhist"][0] == 2) and int(v["vmax"][0]) == ne - 1
+    v2 = O.vline_hist(y, 1, 1, np.array([0.0], np.float32), loi=True)
+    assert int(v2["vhist"][0, ne - 1]) == ne and int(v2["vhist"][0, :ne - 1].sum()) == 0
+    lt = O.lam_tt(v["vhist"], np.array([ne * (ne - 1) // 2]), (2,), ne)
+    assert lt["lam"][0, 0] == (ne * (ne - 1) - 2) / (ne * (ne - 1))
+    assert lt["tt"][0, 0] == (ne * (ne - 1) - 2) / (2 * (ne - 2))
