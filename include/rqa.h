@@ -265,6 +265,41 @@ int rqa_line_measures(rqa_ctx *ctx, const rqa_batch *batch, int32_t K, const uin
                       const int64_t *hist_offsets, const int32_t *lmin, int32_t n_lmin,
                       double *L_out, double *entr_out, double *L_avg, double *entr_avg);
 
+/*
+ * Vertical lines of the whole Ne x Ne recurrence matrix (both triangles), the
+ * input of laminarity and trapping time: V_k(l) = number of maximal runs of
+ * length l of recurrent cells along a column (Sect. 2 extends the averaging
+ * to other RQA measures; definitions as usual in RQA).  The cell (j, j) ends
+ * a run, unless the context has RQA_FLAG_LOI, where it is recurrent.
+ *   eps          device, S*K FP32, ascending within each series
+ *   vhist        device uint64, packed per series as [k][l-1], l = 1..Ne-1
+ *                (l = 1..Ne with RQA_FLAG_LOI); overwritten; may be NULL
+ *   vhist_offsets host, S+1: vhist_offsets[s+1]-vhist_offsets[s] must be
+ *                K*(Ne_s-1) (K*Ne_s with RQA_FLAG_LOI), else RQA_ERR_CAPACITY
+ *   vmax         device, S*K uint32, longest vertical line (may be NULL)
+ *   vmass        device, S*K uint64, sum of l V_k(l): every recurrent cell of
+ *                the matrix, 2 C_k (+ Ne with RQA_FLAG_LOI) (may be NULL)
+ * One sweep over every cell of the matrix per group of at most 31 targets
+ * (2P + Ne cells: about twice the diagonal line pass).
+ */
+int rqa_vline_hist(rqa_ctx *ctx, const rqa_batch *batch, const float *eps, int32_t K,
+                   uint64_t *vhist, const int64_t *vhist_offsets, uint32_t *vmax, uint64_t *vmass);
+
+/*
+ * Laminarity and trapping time from vertical-line histograms, per target and
+ * averaged over the targets (mean in k order, like DET):
+ *   LAM = sum_{l >= vmin} l V_k(l) / sum_{l >= 1} l V_k(l)
+ *   TT  = sum_{l >= vmin} l V_k(l) / sum_{l >= vmin} V_k(l)   (NaN: no line)
+ * FP64 ratios of exact integer sums.
+ *   vhist, vhist_offsets  as written by rqa_vline_hist (same context flags)
+ *   vmin         host, n_vmin (1..RQA_LMIN_MAX) minimal lengths, each >= 1
+ *   lam_out, tt_out   device, S*K*n_vmin FP64 (may be NULL)
+ *   lam_avg, tt_avg   device, S*n_vmin FP64 (may be NULL)
+ */
+int rqa_lam_tt(rqa_ctx *ctx, const rqa_batch *batch, int32_t K, const uint64_t *vhist,
+               const int64_t *vhist_offsets, const int32_t *vmin, int32_t n_vmin, double *lam_out,
+               double *tt_out, double *lam_avg, double *tt_avg);
+
 /* ---- selection without allocation ---------------------------------------
  *
  * The paper has no counterpart to this entry point; it exists for callers

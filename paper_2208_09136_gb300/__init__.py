@@ -22,6 +22,7 @@ from .abi import (  # noqa: F401
     rqa_bracket_stats, RQA_MLP_PARAMS, RQA_MLP_ACTS, RQA_MLP_OUT,
     rqa_eps_for_rr_noalloc, RQA_NOALLOC_MAX_SERIES,
     rqa_graph_replays, rqa_autotune, RQA_FLAG_NO_GRAPHS, RQA_FLAG_LOI, rqa_line_measures,
+    rqa_vline_hist, rqa_lam_tt,
     RQA_SCHED_BATCHED, RQA_SCHED_PER_SERIES, RQA_SELECT_AUTO, RQA_SELECT_BRACKET,
     RQA_SELECT_RADIX, RQA_K_MAX, RQA_LMIN_MAX, RQA_FEATURES,
 )
@@ -79,6 +80,43 @@ def line_measures(ctx: Context, batch: Batch, hist, hist_offsets, K: int,
            "entr_avg": torch.empty((S, len(lmin)), dtype=torch.float64, device=dev)}
     rqa_line_measures(ctx, batch, K, hist, hist_offsets, lmin, out["L"], out["entr"], out["L_avg"],
                       out["entr_avg"])
+    return out
+
+
+def vline_offsets(batch: Batch, K: int, loi: bool = False) -> np.ndarray:
+    """Packed offsets of vertical-line histograms: K*(Ne-1) per series, K*Ne
+    when the context counts the line of identity."""
+    off = np.zeros(batch.n_series + 1, dtype=np.int64)
+    off[1:] = np.cumsum(K * (batch.ne - 1 + (1 if loi else 0)))
+    return off
+
+
+def vline_hist(ctx: Context, batch: Batch, eps, K: int, loi: bool = False) -> Dict[str, "object"]:
+    """Vertical-line histograms V_k(l) (packed), longest vertical line and
+    vertical mass per target."""
+    import torch
+    S = batch.n_series
+    dev = batch.y.device
+    voff = vline_offsets(batch, K, loi)
+    out = {"vhist": torch.empty(int(voff[-1]), dtype=torch.uint64, device=dev), "vhist_offsets": voff,
+           "vmax": torch.empty((S, K), dtype=torch.uint32, device=dev),
+           "vmass": torch.empty((S, K), dtype=torch.uint64, device=dev)}
+    rqa_vline_hist(ctx, batch, eps, K, out["vhist"], voff, out["vmax"], out["vmass"])
+    return out
+
+
+def lam_tt(ctx: Context, batch: Batch, vhist, vhist_offsets, K: int,
+           vmin: Sequence[int] = (2,)) -> Dict[str, "object"]:
+    """Laminarity and trapping time per target (S, K, V) and their means (S, V)."""
+    import torch
+    S = batch.n_series
+    dev = batch.y.device
+    out = {"lam": torch.empty((S, K, len(vmin)), dtype=torch.float64, device=dev),
+           "tt": torch.empty((S, K, len(vmin)), dtype=torch.float64, device=dev),
+           "lam_avg": torch.empty((S, len(vmin)), dtype=torch.float64, device=dev),
+           "tt_avg": torch.empty((S, len(vmin)), dtype=torch.float64, device=dev)}
+    rqa_lam_tt(ctx, batch, K, vhist, vhist_offsets, vmin, out["lam"], out["tt"], out["lam_avg"],
+               out["tt_avg"])
     return out
 
 

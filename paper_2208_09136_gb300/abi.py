@@ -76,6 +76,9 @@ _SIGS = {
     "rqa_graph_replays": ([c_vp], c_u64),
     "rqa_line_measures": ([c_vp, ctypes.POINTER(_Batch), c_i32, c_vp, c_vp, c_vp, c_i32, c_vp, c_vp,
                            c_vp, c_vp], c_int),
+    "rqa_vline_hist": ([c_vp, ctypes.POINTER(_Batch), c_vp, c_i32, c_vp, c_vp, c_vp, c_vp], c_int),
+    "rqa_lam_tt": ([c_vp, ctypes.POINTER(_Batch), c_i32, c_vp, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp,
+                    c_vp], c_int),
     "rqa_autotune": ([c_vp, ctypes.POINTER(_Batch), c_vp, c_i32, c_i32, c_vp], c_int),
     "rqa_line_hist": ([c_vp, ctypes.POINTER(_Batch), c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp],
                       c_int),
@@ -318,6 +321,36 @@ def rqa_line_measures(ctx: Context, batch: Batch, K: int, hist, hist_offsets, lm
                                    _dev_ptr(L_avg, torch.float64, S * len(lm), "L_avg"),
                                    _dev_ptr(entr_avg, torch.float64, S * len(lm), "entr_avg")),
            "rqa_line_measures")
+
+
+def rqa_vline_hist(ctx: Context, batch: Batch, eps, K: int, vhist=None, vhist_offsets=None,
+                   vmax=None, vmass=None):
+    import torch
+    S = batch.n_series
+    hoff = None if vhist_offsets is None else np.ascontiguousarray(vhist_offsets, dtype=np.int64)
+    b = batch._c()
+    _check(lib().rqa_vline_hist(ctx.handle, ctypes.byref(b), _dev_ptr(eps, torch.float32, S * K, "eps"),
+                                int(K),
+                                _dev_ptr(vhist, torch.uint64, None if hoff is None else int(hoff[-1]), "vhist"),
+                                None if hoff is None else _np_ptr(hoff),
+                                _dev_ptr(vmax, torch.uint32, S * K, "vmax"),
+                                _dev_ptr(vmass, torch.uint64, S * K, "vmass")), "rqa_vline_hist")
+
+
+def rqa_lam_tt(ctx: Context, batch: Batch, K: int, vhist, vhist_offsets, vmin, lam_out=None,
+               tt_out=None, lam_avg=None, tt_avg=None):
+    import torch
+    S = batch.n_series
+    vm = np.ascontiguousarray(vmin, dtype=np.int32)
+    hoff = np.ascontiguousarray(vhist_offsets, dtype=np.int64)
+    b = batch._c()
+    n = S * K * len(vm)
+    _check(lib().rqa_lam_tt(ctx.handle, ctypes.byref(b), int(K),
+                            _dev_ptr(vhist, torch.uint64, int(hoff[-1]), "vhist"), _np_ptr(hoff),
+                            _np_ptr(vm), len(vm), _dev_ptr(lam_out, torch.float64, n, "lam_out"),
+                            _dev_ptr(tt_out, torch.float64, n, "tt_out"),
+                            _dev_ptr(lam_avg, torch.float64, S * len(vm), "lam_avg"),
+                            _dev_ptr(tt_avg, torch.float64, S * len(vm), "tt_avg")), "rqa_lam_tt")
 
 
 def rqa_graph_replays(ctx: Context) -> int:

@@ -568,7 +568,7 @@ int ensure_line_bufs(rqa_ctx *c, int S, int K)
 
 // The line pass over every series; fills count / lmax / hshort (and hist).
 int run_lines(rqa_ctx *c, const Plan &pl, const float *eps, uint64_t *hist, const int64_t *d_hoff,
-              LineBufs &lb)
+              LineBufs &lb, bool vert = false)
 {
     const int S = pl.S, K = pl.K;
     const size_t sk = (size_t)S * K;
@@ -579,6 +579,7 @@ int run_lines(rqa_ctx *c, const Plan &pl, const float *eps, uint64_t *hist, cons
     lb.hist = hist;
     lb.hist_off = d_hoff;
     lb.kstride = K;
+    lb.loi = vert && c->loi;  // only vertical lines run through the identity cells
     if (int rc = check_cuda(cudaMemsetAsync(lb.count, 0, sk * 8, c->stream))) return rc;
     if (int rc = check_cuda(cudaMemsetAsync(lb.lmax, 0, sk * 4, c->stream))) return rc;
     if (int rc = check_cuda(cudaMemsetAsync(lb.hshort, 0, sk * LSH * 8, c->stream))) return rc;
@@ -600,8 +601,10 @@ int run_lines(rqa_ctx *c, const Plan &pl, const float *eps, uint64_t *hist, cons
             lb.k0 = g * gsz;
             a.queue = q;
             q += 16;
-            if (int rc = launched(c, launch_lines(a, lb, std::min(gsz, K - lb.k0), grid_for(a.n_units),
-                                                  pl.mt, c->stream)))
+            const int kg = std::min(gsz, K - lb.k0);
+            const int grid = grid_for(a.n_units);
+            if (int rc = launched(c, vert ? launch_vlines(a, lb, kg, grid, pl.mt, c->stream)
+                                          : launch_lines(a, lb, kg, grid, pl.mt, c->stream)))
                 return rc;
         }
         return RQA_OK;
@@ -661,14 +664,14 @@ int line_outputs_tail(rqa_ctx *c, const Plan &pl, const rqa_line_outputs *lo, Li
     return RQA_OK;
 }
 
-int validate_hist(const rqa_batch *b, int K, const uint64_t *hist, const int64_t *hoff)
+int validate_hist(const rqa_batch *b, int K, const uint64_t *hist, const int64_t *hoff, int extra = 0)
 {
     if (!hist) return RQA_OK;
     if (!hoff) return RQA_ERR_INVALID_ARG;
     if (hoff[0] != 0) return RQA_ERR_CAPACITY;
     for (int s = 0; s < b->n_series; ++s) {
         const int64_t ne = (b->offsets[s + 1] - b->offsets[s]) - (int64_t)(b->m[s] - 1) * b->tau[s];
-        if (hoff[s + 1] - hoff[s] != (int64_t)K * (ne - 1)) return RQA_ERR_CAPACITY;
+        if (hoff[s + 1] - hoff[s] != (int64_t)K * (ne - 1 + extra)) return RQA_ERR_CAPACITY;
     }
     return RQA_OK;
 }
@@ -1000,6 +1003,69 @@ int rqa_line_measures(rqa_ctx *c, const rqa_batch *b, int32_t K, const uint64_t 
     if (int rc = upload_plan(c, pl, lmin, n_lmin, hist_offsets)) return rc;
     return launched(c, launch_line_measures(hist, pl.d_hoff, pl.S, K, pl.d_lmin, n_lmin, L, E, L_avg,
                                             entr_avg, c->loi, c->stream));
+}
+
+int rqa_vline_hist(rqa_ctx *c, const rqa_batch *b, const float *eps, int32_t K, uint64_t *vhist,
+                   const int64_t *vhist_offsets, uint32_t *vmax, uint64_t *vmass)
+{
+    if (!c || !eps || K < 1 || K > RQA_K_MAX) return RQA_ERR_INVALID_ARG;
+    if (int rc = validate_batch(b)) return rc;
+    if (int rc = validate_hist(b, K, vhist, vhist_offsets, c->loi ? 1 : 0)) return rc;
+    cudaSetDevice(c->device);
+    // the vertical pass walks bands of DL_DEFAULT columns: a plan for that width
+    const int saved = c->band_lines;
+    c->band_lines = DL_DEFAULT;
+    Plan pl;
+    const int rcp = make_plan(c, b, nullptr, 0, K, pl);
+    c->band_lines = saved;
+    if (rcp) return rcp;
+    if (int rc = ensure_line_bufs(c, pl.S, K)) return rc;
+    if (int rc = upload_plan(c, pl, nullptr, 0, vhist ? vhist_offsets : nullptr)) return rc;
+    if (int rc = launched(c, launch_check_finite(b->y, pl.total, P<int>(c->status), c->stream)))
+        return rc;
+    if (vhist)
+        if (int rc = check_cuda(cudaMemsetAsync(vhist, 0, (size_t)vhist_offsets[pl.S] * 8, c->stream)))
+            return rc;
+    LineBufs lb{};
+    if (int rc = run_lines(c, pl, eps, vhist, vhist ? pl.d_hoff : nullptr, lb, true)) return rc;
+    lb.loi = c->loi;
+    if (vhist)
+        if (int rc = launched(c, launch_finalize_hist(lb, pl.d_sd, pl.S, K, nullptr, c->stream)))
+            return rc;
+    const size_t sk = (size_t)pl.S * K;
+    if (vmax)
+        if (int rc = check_cuda(cudaMemcpyAsync(vmax, lb.lmax, sk * 4, cudaMemcpyDeviceToDevice, c->stream)))
+            return rc;
+    if (vmass)
+        if (int rc = check_cuda(cudaMemcpyAsync(vmass, lb.count, sk * 8, cudaMemcpyDeviceToDevice, c->stream)))
+            return rc;
+    return RQA_OK;
+}
+
+int rqa_lam_tt(rqa_ctx *c, const rqa_batch *b, int32_t K, const uint64_t *vhist,
+               const int64_t *vhist_offsets, const int32_t *vmin, int32_t n_vmin, double *lam_out,
+               double *tt_out, double *lam_avg, double *tt_avg)
+{
+    if (!c || !vhist || !vmin || n_vmin < 1 || n_vmin > RQA_LMIN_MAX || K < 1 || K > RQA_K_MAX)
+        return RQA_ERR_INVALID_ARG;
+    for (int j = 0; j < n_vmin; ++j)
+        if (vmin[j] < 1) return RQA_ERR_INVALID_ARG;
+    if (int rc = validate_batch(b)) return rc;
+    if (int rc = validate_hist(b, K, vhist, vhist_offsets, c->loi ? 1 : 0)) return rc;
+    if (!lam_out && !tt_out && !lam_avg && !tt_avg) return RQA_OK;
+    cudaSetDevice(c->device);
+    Plan pl;
+    if (int rc = make_plan(c, b, nullptr, 0, K, pl)) return rc;
+    const size_t n = (size_t)pl.S * K * n_vmin;
+    double *lam = lam_out, *tt = tt_out;
+    if ((lam_avg && !lam) || (tt_avg && !tt)) {
+        if (int rc = ensure(c->meas, 2 * n * sizeof(double))) return rc;
+        if (lam_avg && !lam) lam = P<double>(c->meas);
+        if (tt_avg && !tt) tt = P<double>(c->meas) + n;
+    }
+    if (int rc = upload_plan(c, pl, vmin, n_vmin, vhist_offsets)) return rc;
+    return launched(c, launch_lam_tt(vhist, pl.d_hoff, pl.S, K, pl.d_lmin, n_vmin, lam, tt, lam_avg,
+                                     tt_avg, c->stream));
 }
 
 int rqa_set_timing(rqa_ctx *c, int enable)

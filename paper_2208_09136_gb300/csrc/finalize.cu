@@ -55,11 +55,12 @@ __global__ void k_finalize_hist(LineBufs lb, const SeriesDev *series, int K, uin
 {
     const int s = blockIdx.x;
     const int ne = series[s].ne;
-    const int nl = min(LSH, ne - 1);
+    const int row = ne - 1 + (lb.loi ? 1 : 0);  // lengths per target (vertical, identity: Ne)
+    const int nl = min(LSH, row);
     for (int x = threadIdx.x; x < K * LSH; x += blockDim.x) {
         const int k = x / LSH, l = x - k * LSH + 1;
         const uint64_t v = lb.hshort[((int64_t)s * K + k) * LSH + (l - 1)];
-        if (lb.hist && l <= nl) lb.hist[lb.hist_off[s] + (int64_t)k * (ne - 1) + (l - 1)] = v;
+        if (lb.hist && l <= nl) lb.hist[lb.hist_off[s] + (int64_t)k * row + (l - 1)] = v;
     }
     if (stencil && threadIdx.x < K) {
         const int64_t o = (int64_t)s * K + threadIdx.x;

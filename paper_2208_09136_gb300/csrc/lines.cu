@@ -145,7 +145,10 @@ int lines_smem_bytes(int) { return LWARPS * warp_smem_words() * 4; }
 
 // Series s and bands [b_lo, b_hi) of work unit u: a unit is a.chunk
 // consecutive bands of one series; units run over the series in a.order
-// (largest first), band 0 (longest diagonals) first.
+// (largest first), band 0 (longest diagonals) first.  The vertical pass uses
+// the same units over bands of columns; a series has ceil(Ne / D) of them,
+// at most one more than of diagonals, which its last unit takes on.
+template <bool VERT>
 __device__ __forceinline__ void unit_of(const CellArgs &a, int64_t u, int &s, int &b_lo,
                                         int &b_hi, const SeriesDev *series)
 {
@@ -157,13 +160,18 @@ __device__ __forceinline__ void unit_of(const CellArgs &a, int64_t u, int &s, in
     }
     s = a.order[lo];
     b_lo = (int)(u - a.uprefix[lo]) * a.chunk;
-    b_hi = min(b_lo + a.chunk, (series[s].ne - 1 + a.band_lines - 1) / a.band_lines);
+    const int nbd = (series[s].ne - 1 + a.band_lines - 1) / a.band_lines;
+    b_hi = min(b_lo + a.chunk, nbd);
+    if (VERT && b_lo + a.chunk >= nbd) b_hi = (series[s].ne + a.band_lines - 1) / a.band_lines;
 }
 
 // Warp-centric: every warp pulls whole bands from one global queue and keeps
 // its own histogram in shared memory, flushed when it moves to another series
 // and at exit.  No CTA-wide barrier, so no warp waits for another.
-template <int D, int M, int TAU, bool HIST>
+// VERT: the vertical pass -- a band is D consecutive columns c, walked over
+// every row i of the matrix (the cell (c, c) ends a line unless lb.loi), and
+// the lines found are vertical ones.
+template <int D, int M, int TAU, bool HIST, bool VERT = false>
 __global__ void __launch_bounds__(LTHREADS, 7) k_lines(CellArgs a, LineBufs lb, int K)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -235,7 +243,7 @@ __global__ void __launch_bounds__(LTHREADS, 7) k_lines(CellArgs a, LineBufs lb, 
         u = __shfl_sync(FULL, u, 0);
         if (u >= a.n_units) break;
         int s, ub_lo, ub_hi;
-        unit_of(a, u, s, ub_lo, ub_hi, a.series);
+        unit_of<VERT>(a, u, s, ub_lo, ub_hi, a.series);
         if (s != cur) {
             flush();
             cur = s;
@@ -287,7 +295,10 @@ __global__ void __launch_bounds__(LTHREADS, 7) k_lines(CellArgs a, LineBufs lb, 
                 }
             }
             if (HIST && klane)
-                sink.hist = lb.hist + lb.hist_off[s] + (int64_t)(lb.k0 + lane) * (sd.ne - 1);
+                // a vertical line may span a whole column (Ne cells) when the
+                // identity cells are recurrent
+                sink.hist = lb.hist + lb.hist_off[s] +
+                            (int64_t)(lb.k0 + lane) * (sd.ne - 1 + (VERT && lb.loi ? 1 : 0));
             sink.gshort = lb.hshort + ((int64_t)s * lb.kstride + lb.k0 + (klane ? lane : 0)) * LSH;
             __syncwarp();
         }
@@ -298,9 +309,10 @@ __global__ void __launch_bounds__(LTHREADS, 7) k_lines(CellArgs a, LineBufs lb, 
         auto bands = [&](auto use_table) {
             constexpr bool TABLE = decltype(use_table)::value;
             for (int b = ub_lo; b < ub_hi; ++b) {
-                int d_lo, d_hi;
-                band_range(b, D, sd.ne, d_lo, d_hi);
-                const int rows = sd.ne - d_lo;
+                int d_lo = 0, d_hi = 0;
+                if (!VERT) band_range(b, D, sd.ne, d_lo, d_hi);
+                const int c_lo = b * D;                      // vertical pass: first column
+                const int rows = VERT ? sd.ne : sd.ne - d_lo;
                 uint32_t carry[D];
 #pragma unroll
                 for (int j = 0; j < D; ++j) carry[j] = 0;
@@ -309,12 +321,20 @@ __global__ void __launch_bounds__(LTHREADS, 7) k_lines(CellArgs a, LineBufs lb, 
                     constexpr bool INTERIOR = decltype(interior)::value;
                     const int i = i0 + lane;
                     BandTile<M, TAU, D> tile;
-                    if (INTERIOR) tile.load_fast(ys, i, d_lo, sd.tau);
-                    else tile.load(ys, sd.n, i, d_lo, rows, sd.tau, sd.m);
+                    if (VERT) {
+                        if (INTERIOR) tile.load_vert_fast(ys, i, c_lo, sd.tau);
+                        else tile.load_vert(ys, sd.n, sd.ne, i, c_lo, sd.tau);
+                    } else {
+                        if (INTERIOR) tile.load_fast(ys, i, d_lo, sd.tau);
+                        else tile.load(ys, sd.n, i, d_lo, rows, sd.tau, sd.m);
+                    }
 #pragma unroll
                     for (int j = 0; j < D; ++j) {
-                        const int dl = d_lo + j;
-                        const bool valid = INTERIOR || i < sd.ne - dl;
+                        // diagonal pass: cell (i, i + dl); vertical: (i, c_lo + j)
+                        const int dl = VERT ? c_lo + j - i : d_lo + j;
+                        const bool valid =
+                            VERT ? (INTERIOR || (i < sd.ne && c_lo + j < sd.ne)) && (lb.loi || dl != 0)
+                                 : INTERIOR || i < sd.ne - dl;
                         uint32_t r = 31;  // outside the diagonal: recurrent for no k
                         // register windows read no memory per cell, so cells
                         // outside the triangle are computed and discarded
@@ -358,7 +378,9 @@ __global__ void __launch_bounds__(LTHREADS, 7) k_lines(CellArgs a, LineBufs lb, 
                 // field could overflow
                 constexpr int SETTLE = 1023 / (15 * D);
                 int i0 = 0, nrb = 0;
-                for (; i0 + 32 <= rows - (D - 1); i0 += 32) {
+                // interior row blocks: every lane's D cells inside the matrix
+                const int i_end = VERT ? (c_lo + D <= sd.ne ? rows - 31 : 0) : rows - (D - 1) - 31;
+                for (; i0 < i_end; i0 += 32) {
                     row_block(i0, std::true_type{});
                     if (++nrb == SETTLE) {
                         sink.settle();
@@ -424,6 +446,44 @@ static cudaError_t launch_lines_h(const CellArgs &a, const LineBufs &lb, int K, 
     grid = persistent_cap(reinterpret_cast<const void *>(kern), smem, grid, LTHREADS);
     kern<<<grid, LTHREADS, smem, st>>>(a, lb, K);
     return cudaGetLastError();
+}
+
+template <bool HIST>
+static cudaError_t launch_vlines_h(const CellArgs &a, const LineBufs &lb, int K, int grid,
+                                   int embed, cudaStream_t st)
+{
+    constexpr int D = DL_DEFAULT;
+    void (*kern)(CellArgs, LineBufs, int) = nullptr;
+    switch (embed) {
+    case E_M1T1: kern = k_lines<D, 1, 1, HIST, true>; break;
+    case E_M3T1: kern = k_lines<D, 3, 1, HIST, true>; break;
+    case E_M3T3: kern = k_lines<D, 3, 3, HIST, true>; break;
+    case E_M1: kern = k_lines<D, 1, 0, HIST, true>; break;
+    case E_M2: kern = k_lines<D, 2, 0, HIST, true>; break;
+    case E_M3: kern = k_lines<D, 3, 0, HIST, true>; break;
+    case E_M4: kern = k_lines<D, 4, 0, HIST, true>; break;
+    default: kern = k_lines<D, 0, 0, HIST, true>; break;
+    }
+    const int smem = lines_smem_bytes(K);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    grid *= WARPS / LWARPS;
+    grid = persistent_cap(reinterpret_cast<const void *>(kern), smem, grid, LTHREADS);
+    kern<<<grid, LTHREADS, smem, st>>>(a, lb, K);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vlines(const CellArgs &a, const LineBufs &lb, int K, int grid, int embed,
+                          cudaStream_t st)
+{
+    const bool hist = lb.hist != nullptr;
+    if (a.band_lines != DL_DEFAULT || !a.y || !a.series || !a.order || !a.uprefix || !a.queue ||
+        !a.status || !lb.eps || !lb.count || !lb.lmax || !lb.hshort || (hist && !lb.hist_off) ||
+        K < 1 || K > LINE_KMAX || lb.k0 < 0 || lb.k0 + K > lb.kstride || grid < 1 || a.n_units < 1 ||
+        a.n_pos < 1)
+        return cudaErrorInvalidValue;
+    return hist ? launch_vlines_h<true>(a, lb, K, grid, embed, st)
+                : launch_vlines_h<false>(a, lb, K, grid, embed, st);
 }
 
 // Band widths the line pass supports for an embedding variant.

@@ -138,3 +138,82 @@ cudaError_t launch_line_measures(const uint64_t *hist, const int64_t *hoff_dev, 
 }
 
 }  // namespace rqa
+
+namespace rqa {
+
+// Laminarity and trapping time from a vertical-line histogram V_k(l)
+// (Marwan et al. 2007, Sect. 5.1; Sect. 2 of the paper extends the RR
+// averaging to such measures):
+//   LAM = sum_{l >= vmin} l V(l) / sum_{l >= 1} l V(l)   (the denominator is
+//         every recurrent cell: each lies on exactly one vertical line)
+//   TT  = sum_{l >= vmin} l V(l) / sum_{l >= vmin} V(l)  (NaN: no such line)
+// FP64 ratios of exact integer sums; one CTA per (series, target).
+__global__ void __launch_bounds__(MT)
+k_lam_tt(const uint64_t *__restrict__ hist, const int64_t *__restrict__ hoff, int K,
+         const int32_t *__restrict__ vmin, int n_vmin, double *lam_out, double *tt_out)
+{
+    __shared__ unsigned long long red[MT / 32][2 * LMIN_MAX + 1];
+    const int s = blockIdx.x / K, k = blockIdx.x - s * K;
+    const int64_t nl = (hoff[s + 1] - hoff[s]) / K;
+    const uint64_t *row = hist + hoff[s] + (int64_t)k * nl;
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    unsigned long long n[LMIN_MAX], m[LMIN_MAX], all = 0ull;
+#pragma unroll
+    for (int j = 0; j < LMIN_MAX; ++j) n[j] = m[j] = 0ull;
+    for (int64_t l = 1 + t; l <= nl; l += MT) {
+        const unsigned long long c = row[l - 1];
+        if (!c) continue;
+        all += c * (unsigned long long)l;
+#pragma unroll
+        for (int j = 0; j < LMIN_MAX; ++j)
+            if (j < n_vmin && l >= vmin[j]) {
+                n[j] += c;
+                m[j] += c * (unsigned long long)l;
+            }
+    }
+    for (int o = 16; o > 0; o >>= 1) all += __shfl_xor_sync(FULL, all, o);
+#pragma unroll
+    for (int j = 0; j < LMIN_MAX; ++j)
+        for (int o = 16; o > 0; o >>= 1) {
+            n[j] += __shfl_xor_sync(FULL, n[j], o);
+            m[j] += __shfl_xor_sync(FULL, m[j], o);
+        }
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < LMIN_MAX; ++j) {
+            red[w][j] = n[j];
+            red[w][LMIN_MAX + j] = m[j];
+        }
+        red[w][2 * LMIN_MAX] = all;
+    }
+    __syncthreads();
+    if (t < n_vmin) {
+        unsigned long long sn = 0, sm = 0, sa = 0;
+        for (int q = 0; q < MT / 32; ++q) {
+            sn += red[q][t];
+            sm += red[q][LMIN_MAX + t];
+            sa += red[q][2 * LMIN_MAX];
+        }
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        const int64_t o = ((int64_t)s * K + k) * n_vmin + t;
+        if (lam_out) lam_out[o] = sa ? (double)sm / (double)sa : nan;
+        if (tt_out) tt_out[o] = sn ? (double)sm / (double)sn : nan;
+    }
+}
+
+cudaError_t launch_lam_tt(const uint64_t *hist, const int64_t *hoff_dev, int S, int K,
+                          const int32_t *vmin_dev, int n_vmin, double *lam_out, double *tt_out,
+                          double *lam_avg, double *tt_avg, cudaStream_t st)
+{
+    if (!hist || !hoff_dev || !vmin_dev || S < 1 || K < 1 || K > KMAX || n_vmin < 1 ||
+        n_vmin > LMIN_MAX || (lam_avg && !lam_out) || (tt_avg && !tt_out))
+        return cudaErrorInvalidValue;
+    k_lam_tt<<<S * K, MT, 0, st>>>(hist, hoff_dev, K, vmin_dev, n_vmin, lam_out, tt_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (lam_avg) k_measure_avg<<<S, 32, 0, st>>>(lam_out, K, n_vmin, lam_avg);
+    if (tt_avg) k_measure_avg<<<S, 32, 0, st>>>(tt_out, K, n_vmin, tt_avg);
+    return cudaGetLastError();
+}
+
+}  // namespace rqa

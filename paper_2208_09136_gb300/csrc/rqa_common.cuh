@@ -47,7 +47,26 @@ struct BandTile {
 #pragma unroll
         for (int x = 0; x < D + (M - 1) * TAU; ++x) w[x] = __ldg(ys + i + d_lo + x);
     }
-    // cell (i, i + d_lo + j); only called for cells inside the triangle
+    // vertical pass: row i, columns c_lo .. c_lo+D-1 (the same window for
+    // every lane); zeros outside the series
+    __device__ __forceinline__ void load_vert(const float *__restrict__ ys, int n, int ne, int i,
+                                              int c_lo, int)
+    {
+#pragma unroll
+        for (int q = 0; q < M; ++q) a[q] = i < ne ? __ldg(ys + i + q * TAU) : 0.f;
+#pragma unroll
+        for (int x = 0; x < D + (M - 1) * TAU; ++x)
+            w[x] = c_lo + x < n ? __ldg(ys + c_lo + x) : 0.f;
+    }
+    __device__ __forceinline__ void load_vert_fast(const float *__restrict__ ys, int i, int c_lo, int)
+    {
+#pragma unroll
+        for (int q = 0; q < M; ++q) a[q] = __ldg(ys + i + q * TAU);
+#pragma unroll
+        for (int x = 0; x < D + (M - 1) * TAU; ++x) w[x] = __ldg(ys + c_lo + x);
+    }
+    // cell (i, i + d_lo + j), or (i, c_lo + j) after load_vert; only called
+    // for cells inside the matrix
     __device__ __forceinline__ float dist(const float *__restrict__, int j, int, int, int,
                                           int) const
     {
@@ -75,6 +94,18 @@ struct BandTile<M, 0, D> {
 #pragma unroll
         for (int q = 0; q < M; ++q) a[q] = __ldg(ys + i + q * tau);
     }
+    __device__ __forceinline__ void load_vert(const float *__restrict__ ys, int, int ne, int i, int,
+                                              int tau)
+    {
+        if (i < ne) {
+#pragma unroll
+            for (int q = 0; q < M; ++q) a[q] = __ldg(ys + i + q * tau);
+        }
+    }
+    __device__ __forceinline__ void load_vert_fast(const float *__restrict__ ys, int i, int, int tau)
+    {
+        load_fast(ys, i, 0, tau);
+    }
     __device__ __forceinline__ float dist(const float *__restrict__ ys, int, int i, int dl,
                                           int tau, int) const
     {
@@ -91,6 +122,8 @@ template <int D>
 struct BandTile<0, 0, D> {
     __device__ __forceinline__ void load(const float *, int, int, int, int, int, int) {}
     __device__ __forceinline__ void load_fast(const float *, int, int, int) {}
+    __device__ __forceinline__ void load_vert(const float *, int, int, int, int, int) {}
+    __device__ __forceinline__ void load_vert_fast(const float *, int, int, int) {}
     __device__ __forceinline__ float dist(const float *__restrict__ ys, int, int i, int dl,
                                           int tau, int m) const
     {

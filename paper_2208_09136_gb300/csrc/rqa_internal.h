@@ -107,9 +107,14 @@ struct LineBufs {
     const int64_t *hist_off;  // device [S+1] offsets into hist (nullptr if no hist)
     int32_t k0;            // line pass: first target of this launch's group
     int32_t kstride;       // targets per series in all arrays above (the call's K)
+    int32_t loi;           // vertical pass: the cells (j, j) are recurrent
 };
 cudaError_t launch_lines(const CellArgs &a, const LineBufs &lb, int K, int grid, int embed,
                          cudaStream_t st);
+// Vertical lines of the whole matrix: the same warp pass over bands of D = 4
+// columns (every row of each), reusing the diagonal pass's work plan.
+cudaError_t launch_vlines(const CellArgs &a, const LineBufs &lb, int K, int grid, int embed,
+                          cudaStream_t st);
 bool lines_band_ok(int embed, int band);
 cudaError_t launch_finalize_det(const LineBufs &lb, const SeriesDev *series, int S, int K,
                                 const int32_t *lmin_dev, int n_lmin, double *det,
@@ -118,6 +123,9 @@ cudaError_t launch_line_measures(const uint64_t *hist, const int64_t *hoff_dev, 
                                  const int32_t *lmin_dev, int n_lmin, double *L_out,
                                  double *E_out, double *L_avg, double *E_avg, bool loi,
                                  cudaStream_t st);
+cudaError_t launch_lam_tt(const uint64_t *hist, const int64_t *hoff_dev, int S, int K,
+                          const int32_t *vmin_dev, int n_vmin, double *lam_out, double *tt_out,
+                          double *lam_avg, double *tt_avg, cudaStream_t st);
 cudaError_t launch_finalize_hist(const LineBufs &lb, const SeriesDev *series, int S, int K,
                                  uint64_t *stencil, cudaStream_t st);
 
