@@ -165,6 +165,43 @@ def line_hist(y: np.ndarray, m: int, tau: int, eps: Sequence[float]) -> Dict[str
     return {"hist": hist, "count": count, "stencil": stencil, "lmax": lmax}
 
 
+def approx_thresholds(y: np.ndarray, n_thr: int = 400) -> np.ndarray:
+    """The fixed threshold grid of the paper's approximate search (described in
+    its source as a comment, Sect. 2): every series mapped onto [0, 1] and RR
+    evaluated at n_thr thresholds.  Reading: thresholds i/n_thr, i = 1..n_thr,
+    of the [0, 1]-normalised series, i.e. in the series' own units
+    thr_i = float32(i) * (range / n_thr) with range = max(y) - min(y), every
+    operation in FP32 (correctly rounded), so any implementation reproduces the
+    grid bit for bit."""
+    y = np.asarray(y, dtype=np.float32)
+    rng = np.float32(np.float32(y.max()) - np.float32(y.min()))
+    scale = np.float32(rng / np.float32(n_thr))
+    return (np.arange(1, n_thr + 1, dtype=np.float32) * scale).astype(np.float32)
+
+
+def eps_approx(y: np.ndarray, m: int, tau: int, rr_num: Sequence[int], rr_den: int,
+               n_thr: int = 400) -> Dict[str, np.ndarray]:
+    """The paper's approximate eps search: RR at every grid threshold
+    (approx_thresholds), then for each target the threshold whose RR is the
+    closest to it (ties: the lower threshold).  Counts over the upper triangle
+    (recurrent iff d <= thr).  Returns eps (FP32), rr (achieved RR, FP64
+    fraction), count (#{d <= eps}) and the full grid counts."""
+    d = np.sort(all_distances(y, m, tau), kind="stable")
+    p = d.shape[0]
+    thr = approx_thresholds(y, n_thr)
+    c = np.searchsorted(d, thr, side="right").astype(np.int64)   # C_j = #{d <= thr_j}
+    eps, rr, cnt = [], [], []
+    for r in rr_num:
+        # |C_j / P - r / den| compared exactly as |C_j den - r P|
+        err = [abs(int(cj) * int(rr_den) - int(r) * int(p)) for cj in c]
+        j = int(np.argmin(err))                                    # first minimum: lower threshold
+        eps.append(thr[j])
+        cnt.append(int(c[j]))
+        rr.append(float(c[j]) / float(p))
+    return {"eps": np.array(eps, dtype=np.float32), "rr": np.array(rr, dtype=np.float64),
+            "count": np.array(cnt, dtype=np.uint64), "grid_count": c.astype(np.uint64), "thr": thr}
+
+
 def column_distances(y: np.ndarray, m: int, tau: int, j: int) -> np.ndarray:
     """d(i, j) for i = 0 .. Ne-1 (the whole column j, d(j, j) = 0), FP32."""
     y = np.asarray(y, dtype=np.float32)

@@ -483,3 +483,40 @@ def test_vertical_lines_constant_series():
     lt = O.lam_tt(v["vhist"], np.array([ne * (ne - 1) // 2]), (2,), ne)
     assert lt["lam"][0, 0] == (ne * (ne - 1) - 2) / (ne * (ne - 1))
     assert lt["tt"][0, 0] == (ne * (ne - 1) - 2) / (2 * (ne - 2))
+
+
+# ------------------------------------------------- the paper's approximate eps search
+def test_approx_grid_and_brute_force():
+    """Grid counts by counting every pair against every grid value, the
+    closest-RR choice by scanning all grid points, and the grid's own
+    definition (i * range / n in FP32)."""
+    rng = np.random.default_rng(3)
+    y = rng.standard_normal(40).astype(np.float32)
+    n_thr = 25
+    r = O.eps_approx(y, 2, 1, [5, 20, 50, 90], 100, n_thr)
+    rg = np.float32(y.max()) - np.float32(y.min())
+    assert np.array_equal(r["thr"], np.float32(np.arange(1, n_thr + 1)) * np.float32(rg / np.float32(n_thr)))
+    ne = 39
+    d = [_d32(y, i, j, 2, 1) for i in range(ne) for j in range(i + 1, ne)]
+    P = len(d)
+    grid = [sum(1 for v in d if v <= t) for t in r["thr"]]
+    assert [int(c) for c in r["grid_count"]] == grid
+    assert grid[-1] == P                                   # the top threshold is the range
+    for k, rr in enumerate([5, 20, 50, 90]):
+        best = min(range(n_thr), key=lambda j: (abs(grid[j] / P - rr / 100), j))
+        assert r["eps"][k] == r["thr"][best] and int(r["count"][k]) == grid[best]
+        assert r["rr"][k] == grid[best] / P
+
+
+def test_approx_error_bound():
+    """The achieved RR is within half a grid step's RR jump of the target."""
+    rng = np.random.default_rng(4)
+    y = np.sin(np.arange(300) * 0.31).astype(np.float32) + 0.1 * rng.standard_normal(300).astype(np.float32)
+    r = O.eps_approx(y, 3, 2, list(range(1, 100)), 100)
+    P = pair = (300 - 4) * (300 - 5) // 2
+    c = np.concatenate(([0], r["grid_count"].astype(np.int64)))
+    for k, rr in enumerate(range(1, 100)):
+        t = rr / 100
+        j = int(np.searchsorted(c / P, t))
+        lo, hi = c[max(j - 1, 0)] / P, c[min(j, len(c) - 1)] / P
+        assert abs(r["rr"][k] - t) <= max(t - lo, hi - t) + 1e-15
