@@ -300,6 +300,23 @@ int rqa_lam_tt(rqa_ctx *ctx, const rqa_batch *batch, int32_t K, const uint64_t *
                const int64_t *vhist_offsets, const int32_t *vmin, int32_t n_vmin, double *lam_out,
                double *tt_out, double *lam_avg, double *tt_avg);
 
+/*
+ * The paper's approximate threshold search, for comparison with the exact
+ * selection (its source describes it in a comment to Sect. 2): every series
+ * mapped onto [0, 1] and RR evaluated at n_thr fixed thresholds; for each
+ * target the threshold whose RR is the closest.  Grid, in the series' own
+ * units (FP32, correctly rounded): thr_i = i * ((max y - min y) / n_thr),
+ * i = 1..n_thr.  Upper triangle, recurrent iff d <= thr (RQA_FLAG_LOI is not
+ * applied here).  Ties in |RR - target| go to the lower threshold.
+ *   rr_num, rr_den, K  as in rqa_eps_for_rr;  n_thr 1..1024 (the paper: 400)
+ *   eps_out    device, S*K FP32, the chosen grid thresholds
+ *   rr_out     device, S*K FP64, their recurrence rates #{d <= eps}/P (may be NULL)
+ *   count_out  device, S*K uint64, #{d <= eps} (may be NULL)
+ * The thresholds may then go to rqa_det_avg (its eps argument) for DET.
+ */
+int rqa_eps_approx(rqa_ctx *ctx, const rqa_batch *batch, const int32_t *rr_num, int32_t rr_den,
+                   int32_t K, int32_t n_thr, float *eps_out, double *rr_out, uint64_t *count_out);
+
 /* ---- selection without allocation ---------------------------------------
  *
  * The paper has no counterpart to this entry point; it exists for callers

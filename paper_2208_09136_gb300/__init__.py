@@ -22,7 +22,7 @@ from .abi import (  # noqa: F401
     rqa_bracket_stats, RQA_MLP_PARAMS, RQA_MLP_ACTS, RQA_MLP_OUT,
     rqa_eps_for_rr_noalloc, RQA_NOALLOC_MAX_SERIES,
     rqa_graph_replays, rqa_autotune, RQA_FLAG_NO_GRAPHS, RQA_FLAG_LOI, rqa_line_measures,
-    rqa_vline_hist, rqa_lam_tt,
+    rqa_vline_hist, rqa_lam_tt, rqa_eps_approx,
     RQA_SCHED_BATCHED, RQA_SCHED_PER_SERIES, RQA_SELECT_AUTO, RQA_SELECT_BRACKET,
     RQA_SELECT_RADIX, RQA_K_MAX, RQA_LMIN_MAX, RQA_FEATURES,
 )
@@ -80,6 +80,20 @@ def line_measures(ctx: Context, batch: Batch, hist, hist_offsets, K: int,
            "entr_avg": torch.empty((S, len(lmin)), dtype=torch.float64, device=dev)}
     rqa_line_measures(ctx, batch, K, hist, hist_offsets, lmin, out["L"], out["entr"], out["L_avg"],
                       out["entr_avg"])
+    return out
+
+
+def eps_approx(ctx: Context, batch: Batch, rr_num: Sequence[int], rr_den: int,
+               n_thr: int = 400) -> Dict[str, "object"]:
+    """The paper's approximate search: grid thresholds closest to each target
+    RR, their rates and counts (S, K)."""
+    import torch
+    S, K = batch.n_series, len(rr_num)
+    dev = batch.y.device
+    out = {"eps": torch.empty((S, K), dtype=torch.float32, device=dev),
+           "rr": torch.empty((S, K), dtype=torch.float64, device=dev),
+           "count": torch.empty((S, K), dtype=torch.uint64, device=dev)}
+    rqa_eps_approx(ctx, batch, rr_num, rr_den, n_thr, out["eps"], out["rr"], out["count"])
     return out
 
 

@@ -76,6 +76,7 @@ _SIGS = {
     "rqa_graph_replays": ([c_vp], c_u64),
     "rqa_line_measures": ([c_vp, ctypes.POINTER(_Batch), c_i32, c_vp, c_vp, c_vp, c_i32, c_vp, c_vp,
                            c_vp, c_vp], c_int),
+    "rqa_eps_approx": ([c_vp, ctypes.POINTER(_Batch), c_vp, c_i32, c_i32, c_i32, c_vp, c_vp, c_vp], c_int),
     "rqa_vline_hist": ([c_vp, ctypes.POINTER(_Batch), c_vp, c_i32, c_vp, c_vp, c_vp, c_vp], c_int),
     "rqa_lam_tt": ([c_vp, ctypes.POINTER(_Batch), c_i32, c_vp, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp,
                     c_vp], c_int),
@@ -321,6 +322,18 @@ def rqa_line_measures(ctx: Context, batch: Batch, K: int, hist, hist_offsets, lm
                                    _dev_ptr(L_avg, torch.float64, S * len(lm), "L_avg"),
                                    _dev_ptr(entr_avg, torch.float64, S * len(lm), "entr_avg")),
            "rqa_line_measures")
+
+
+def rqa_eps_approx(ctx: Context, batch: Batch, rr_num, rr_den: int, n_thr: int, eps_out, rr_out=None,
+                   count_out=None):
+    import torch
+    rr = np.ascontiguousarray(rr_num, dtype=np.int32)
+    S, K = batch.n_series, len(rr)
+    b = batch._c()
+    _check(lib().rqa_eps_approx(ctx.handle, ctypes.byref(b), _np_ptr(rr), int(rr_den), K, int(n_thr),
+                                _dev_ptr(eps_out, torch.float32, S * K, "eps_out"),
+                                _dev_ptr(rr_out, torch.float64, S * K, "rr_out"),
+                                _dev_ptr(count_out, torch.uint64, S * K, "count_out")), "rqa_eps_approx")
 
 
 def rqa_vline_hist(ctx: Context, batch: Batch, eps, K: int, vhist=None, vhist_offsets=None,

@@ -66,6 +66,7 @@ struct rqa_ctx {
     DevBuf queue, status;
     DevBuf eps_tmp, le_tmp, lt_tmp, count, lmax, hshort;
     DevBuf meas;  // per-target L / ENTR when only their averages are asked for
+    DevBuf grid_thr, grid_hist, grid_rr;  // the approximate grid search
 
     // learned bracket
     DevBuf mlp;                 // installed network parameters
@@ -784,7 +785,7 @@ void rqa_destroy(rqa_ctx *c)
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->arena, &c->prefix, &c->level, &c->rank, &c->below, &c->tab_sub,
                       &c->tab_mid, &c->tab_fin1, &c->tab_fin2, &c->tab_hash, &c->ngroups, &c->hist,
-                      &c->krange, &c->meas,
+                      &c->krange, &c->meas, &c->grid_thr, &c->grid_hist, &c->grid_rr,
                       &c->redo,
                       &c->queue,
                       &c->status, &c->eps_tmp, &c->le_tmp, &c->lt_tmp, &c->count, &c->lmax,
@@ -1066,6 +1067,46 @@ int rqa_lam_tt(rqa_ctx *c, const rqa_batch *b, int32_t K, const uint64_t *vhist,
     if (int rc = upload_plan(c, pl, vmin, n_vmin, vhist_offsets)) return rc;
     return launched(c, launch_lam_tt(vhist, pl.d_hoff, pl.S, K, pl.d_lmin, n_vmin, lam, tt, lam_avg,
                                      tt_avg, c->stream));
+}
+
+int rqa_eps_approx(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_den, int32_t K,
+                   int32_t n_thr, float *eps_out, double *rr_out, uint64_t *count_out)
+{
+    if (!c || !eps_out || n_thr < 1 || n_thr > 1024) return RQA_ERR_INVALID_ARG;
+    if (int rc = validate_batch(b)) return rc;
+    if (int rc = validate_rr(rr_num, rr_den, K)) return rc;
+    cudaSetDevice(c->device);
+    const bool loi = c->loi;
+    c->loi = false;  // the grid search counts the upper triangle only
+    Plan pl;
+    const int rcp = make_plan(c, b, rr_num, rr_den, K, pl);
+    c->loi = loi;
+    if (rcp) return rcp;
+    if (int rc = upload_plan(c, pl, nullptr, 0, nullptr)) return rc;
+    if (int rc = ensure(c->grid_thr, (size_t)pl.S * n_thr * 4)) return rc;
+    if (int rc = ensure(c->grid_hist, (size_t)pl.S * (n_thr + 1) * 8)) return rc;
+    if (int rc = ensure(c->grid_rr, (size_t)K * 4)) return rc;
+    if (int rc = check_cuda(cudaMemcpyAsync(c->grid_rr.p, rr_num, (size_t)K * 4, cudaMemcpyHostToDevice,
+                                            c->stream)))
+        return rc;
+    if (int rc = check_cuda(cudaMemsetAsync(c->grid_hist.p, 0, (size_t)pl.S * (n_thr + 1) * 8, c->stream)))
+        return rc;
+    if (int rc = launched(c, launch_check_finite(b->y, pl.total, P<int>(c->status), c->stream)))
+        return rc;
+    unsigned *q = nullptr;
+    if (int rc = reset_queue(c, 1, &q)) return rc;
+    CellArgs a{};
+    a.y = pl.y;
+    a.series = pl.d_sd;
+    a.items = pl.d_lpt;
+    a.n_items = (int)pl.items_lpt.size();
+    a.band = c->band;
+    a.queue = q;
+    a.status = P<int>(c->status);
+    c->launches += 2;  // grid and selection kernels
+    return launched(c, launch_grid_select(a, pl.S, n_thr, P<float>(c->grid_thr), P<uint64_t>(c->grid_hist),
+                                          P<int32_t>(c->grid_rr), rr_den, K, eps_out, rr_out, count_out,
+                                          persistent_grid(c, (size_t)a.n_items), pl.mt, c->stream));
 }
 
 int rqa_set_timing(rqa_ctx *c, int enable)

@@ -123,6 +123,10 @@ cudaError_t launch_line_measures(const uint64_t *hist, const int64_t *hoff_dev, 
                                  const int32_t *lmin_dev, int n_lmin, double *L_out,
                                  double *E_out, double *L_avg, double *E_avg, bool loi,
                                  cudaStream_t st);
+cudaError_t launch_grid_select(const CellArgs &a, int S, int n_thr, float *thr, uint64_t *hist,
+                               const int32_t *rr_num_dev, int rr_den, int K, float *eps_out,
+                               double *rr_out, uint64_t *count_out, int grid, int embed,
+                               cudaStream_t st);
 cudaError_t launch_lam_tt(const uint64_t *hist, const int64_t *hoff_dev, int S, int K,
                           const int32_t *vmin_dev, int n_vmin, double *lam_out, double *tt_out,
                           double *lam_avg, double *tt_avg, cudaStream_t st);
