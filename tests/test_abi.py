@@ -85,3 +85,14 @@ def test_null_context_is_rejected(built):
     assert L.rqa_line_hist(None, None, None, 20, None, None, None, None, None) == 1
     assert L.rqa_set_timing(None, 1) == 1
     assert L.rqa_kernel_launches(None) == 0
+
+
+def test_binding_constants_match_header():
+    """Every #define of include/rqa.h that the binding mirrors has its value."""
+    import paper_2208_09136_gb300.abi as abi
+    text = open(os.path.join(ROOT, "include", "rqa.h")).read()
+    defines = {k: int(v) for k, v in re.findall(r"#define\s+(RQA_[A-Z0-9_]+)\s+(\d+)", text)}
+    mirrored = [k for k in defines if hasattr(abi, k)]
+    assert {"RQA_K_MAX", "RQA_FLAG_NO_GRAPHS", "RQA_FLAG_LOI", "RQA_NOALLOC_K_MAX"} <= set(mirrored)
+    for k in mirrored:
+        assert getattr(abi, k) == defines[k], k
