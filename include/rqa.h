@@ -177,6 +177,14 @@ int rqa_autotune(rqa_ctx *ctx, const rqa_batch *batch, const int32_t *rr_num, in
 int rqa_target_counts(uint64_t P, const int32_t *rr_num, int32_t rr_den, int32_t K,
                       uint64_t *T_out);
 
+/* The same with the line of identity counted (RQA_FLAG_LOI; Eq. 3 over the
+ * whole Ne x Ne matrix): T_k = ceil((ceil(rr_num Ne^2 / rr_den) - Ne) / 2),
+ * the upper-triangle cells that reach the rate.  RQA_ERR_INVALID_ARG when the
+ * identity line alone reaches a rate (T_k <= 0), for Ne < 2 or Ne > 2^32.
+ * Host pointers. */
+int rqa_target_counts_loi(uint64_t Ne, const int32_t *rr_num, int32_t rr_den, int32_t K,
+                          uint64_t *T_out);
+
 /* ---- the hot path -------------------------------------------------------- */
 
 /*

@@ -17,6 +17,7 @@ from .abi import (  # noqa: F401
     Batch, Context, RqaError, exported_symbols, lib,
     rqa_abi_version, rqa_create, rqa_destroy, rqa_det_avg, rqa_device_info,
     rqa_error_string, rqa_eps_for_rr, rqa_line_hist, rqa_status, rqa_target_counts,
+    rqa_target_counts_loi,
     rqa_set_timing, rqa_phase_times, rqa_kernel_launches,
     rqa_sketch, rqa_mlp_forward, rqa_mlp_backward, rqa_adam_step, rqa_set_bracket_model,
     rqa_bracket_stats, RQA_MLP_PARAMS, RQA_MLP_ACTS, RQA_MLP_OUT,

@@ -67,6 +67,7 @@ _SIGS = {
     "rqa_status": ([c_vp], c_int),
     "rqa_device_info": ([c_vp, c_vp, c_vp, c_vp], c_int),
     "rqa_target_counts": ([c_u64, c_vp, c_i32, c_i32, c_vp], c_int),
+    "rqa_target_counts_loi": ([c_u64, c_vp, c_i32, c_i32, c_vp], c_int),
     "rqa_eps_for_rr": ([c_vp, ctypes.POINTER(_Batch), c_vp, c_i32, c_i32, c_vp, c_vp, c_vp], c_int),
     "rqa_det_avg": ([c_vp, ctypes.POINTER(_Batch), c_vp, c_i32, c_vp, c_i32, c_vp, c_i32, c_vp,
                      c_vp, c_vp, ctypes.POINTER(_LineOutputs)], c_int),
@@ -254,6 +255,14 @@ def rqa_target_counts(P: int, rr_num: Sequence[int], rr_den: int) -> np.ndarray:
     out = np.zeros(len(rr), dtype=np.uint64)
     _check(lib().rqa_target_counts(int(P), _np_ptr(rr), int(rr_den), len(rr), _np_ptr(out)),
            "rqa_target_counts")
+    return out
+
+
+def rqa_target_counts_loi(ne: int, rr_num: Sequence[int], rr_den: int) -> np.ndarray:
+    rr = np.ascontiguousarray(rr_num, dtype=np.int32)
+    out = np.zeros(len(rr), dtype=np.uint64)
+    _check(lib().rqa_target_counts_loi(int(ne), _np_ptr(rr), int(rr_den), len(rr), _np_ptr(out)),
+           "rqa_target_counts_loi")
     return out
 
 

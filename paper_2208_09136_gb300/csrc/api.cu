@@ -255,16 +255,9 @@ int make_plan(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_
             uint64_t *T = &pl.T[(size_t)s * K];
             if (rqa_target_counts(pl.sd[s].P, rr_num, rr_den, K, T) != RQA_OK)
                 return RQA_ERR_INVALID_ARG;
-            if (c->loi) {  // whole matrix: 2 C + Ne >= ceil(rr Ne^2 / den)
-                const unsigned __int128 ne = (unsigned __int128)(uint64_t)pl.sd[s].ne;
-                for (int k = 0; k < K; ++k) {
-                    const unsigned __int128 full =
-                        ((unsigned __int128)(uint64_t)rr_num[k] * ne * ne + (unsigned)(rr_den - 1)) /
-                        (unsigned)rr_den;
-                    if (full <= ne) return RQA_ERR_INVALID_ARG;  // the identity line alone reaches it
-                    T[k] = (uint64_t)((full - ne + 1) / 2);
-                }
-            }
+            if (c->loi)  // whole matrix: 2 C + Ne >= ceil(rr Ne^2 / den)
+                if (rqa_target_counts_loi((uint64_t)pl.sd[s].ne, rr_num, rr_den, K, T) != RQA_OK)
+                    return RQA_ERR_INVALID_ARG;
         }
     }
     // CTA work items (counting rounds): runs of consecutive bands of one
@@ -723,6 +716,22 @@ int rqa_target_counts(uint64_t Pc, const int32_t *rr_num, int32_t rr_den, int32_
         const unsigned __int128 num = (unsigned __int128)(uint64_t)rr_num[k] * Pc;
         const unsigned __int128 t = (num + (unsigned __int128)(rr_den - 1)) / (unsigned)rr_den;
         T_out[k] = (uint64_t)t;
+    }
+    return RQA_OK;
+}
+
+int rqa_target_counts_loi(uint64_t ne, const int32_t *rr_num, int32_t rr_den, int32_t K,
+                          uint64_t *T_out)
+{
+    if (!rr_num || !T_out || K < 1 || rr_den < 1 || ne < 2 || ne > ((uint64_t)1 << 32))
+        return RQA_ERR_INVALID_ARG;
+    for (int k = 0; k < K; ++k) {
+        if (rr_num[k] < 1 || rr_num[k] >= rr_den) return RQA_ERR_INVALID_ARG;
+        const unsigned __int128 n = ne;
+        const unsigned __int128 full =
+            ((unsigned __int128)(uint64_t)rr_num[k] * n * n + (unsigned)(rr_den - 1)) / (unsigned)rr_den;
+        if (full <= n) return RQA_ERR_INVALID_ARG;  // the identity line alone reaches this rate
+        T_out[k] = (uint64_t)((full - n + 1) / 2);
     }
     return RQA_OK;
 }

@@ -96,3 +96,21 @@ def test_binding_constants_match_header():
     assert {"RQA_K_MAX", "RQA_FLAG_NO_GRAPHS", "RQA_FLAG_LOI", "RQA_NOALLOC_K_MAX"} <= set(mirrored)
     for k in mirrored:
         assert getattr(abi, k) == defines[k], k
+
+
+@pytest.mark.parametrize("ne", [2, 11, 100, 101, 4998, 99994, 1 << 31, 1 << 32])
+def test_target_counts_loi_match_oracle(built, ne):
+    """The identity-line targets (RQA_FLAG_LOI) of the library's host code equal
+    the oracle's; rates the identity line reaches alone are rejected by both."""
+    import paper_2208_09136_gb300 as rqa
+    from oracle import rqa_oracle as O
+    for rr, den in [(list(range(1, 100)), 100), ([1, 5, 127], 128), ([1, 2], 3)]:
+        try:
+            want = O.target_counts_loi(ne, rr, den)
+        except ValueError:
+            with pytest.raises(rqa.RqaError):
+                rqa.rqa_target_counts_loi(ne, rr, den)
+            continue
+        assert np.array_equal(rqa.rqa_target_counts_loi(ne, rr, den), want)
+    with pytest.raises(rqa.RqaError):
+        rqa.rqa_target_counts_loi((1 << 32) + 1, [50], 100)
