@@ -21,9 +21,9 @@
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
+#endif
 
 #define ORC_KMAX 128 /* thresholds per call (capacity of the per-thread arrays) */
-#endif
 
 static inline float orc_dist(const float *y, int64_t i, int64_t j, int m, int tau)
 {

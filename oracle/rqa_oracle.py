@@ -270,6 +270,8 @@ def det_from_hist(hist: np.ndarray, count: np.ndarray, lmin: Sequence[int],
                   loi: bool = False) -> np.ndarray:
     """DET_k(lmin) = sum_{l >= lmin} l P_k(l) / C_k in FP64 (Eq. 4).
 
+    With no recurrent cell (C_k = 0, only possible for thresholds the caller
+    gives) Eq. 4 is 0/0: undefined, returned as NaN (the IEEE quotient 0.0/0.0).
     loi: over the whole matrix with the line of identity, as Eq. 4 is written:
     every upper-triangle line twice plus the identity line of length Ne =
     hist.shape[1] + 1, i.e. (2 sum_{l >= lmin} l P_k(l) + Ne [Ne >= lmin]) /
@@ -287,7 +289,7 @@ def det_from_hist(hist: np.ndarray, count: np.ndarray, lmin: Sequence[int],
             if loi:
                 num = 2 * num + (ne if ne >= lm else 0)
                 den = 2 * den + ne
-            out[kk, j] = float(num) / float(den)
+            out[kk, j] = float(num) / float(den) if den else float("nan")
     return out
 
 

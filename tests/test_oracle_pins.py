@@ -520,3 +520,39 @@ def test_approx_error_bound():
         j = int(np.searchsorted(c / P, t))
         lo, hi = c[max(j - 1, 0)] / P, c[min(j, len(c) - 1)] / P
         assert abs(r["rr"][k] - t) <= max(t - lo, hi - t) + 1e-15
+
+
+def test_det_undefined_without_recurrences():
+    """Thresholds below the smallest distance leave no recurrent cell: Eq. 4 is
+    then 0/0, which the oracle returns as NaN (the IEEE quotient); the average
+    over the targets is NaN too.  The smallest distance is taken by brute force
+    over all pairs, independent of the oracle's own distance routine."""
+    y = np.array([0.0, 1.0, 3.0, 7.0, 15.0, 31.0], dtype=np.float32)  # distinct gaps
+    dmin = min(abs(float(y[i]) - float(y[j])) for i in range(len(y)) for j in range(i + 1, len(y)))
+    assert dmin == 1.0
+    eps = np.array([0.5, 2.0], dtype=np.float32)  # below dmin, then above it
+    lines = O.line_hist(y, 1, 1, eps)
+    assert int(lines["count"][0]) == 0 and int(lines["hist"][0].sum()) == 0
+    det = O.det_from_hist(lines["hist"], lines["count"], (2, 3))
+    assert np.isnan(det[0]).all()
+    # the second threshold: cells with d <= 2 are (0,1) and (1,2): one line of
+    # length 2 on the first diagonal, so DET_2 = 2/2 and DET_3 = 0/2
+    assert int(lines["count"][1]) == 2
+    assert det[1].tolist() == [1.0, 0.0]
+    assert np.isnan(O.det_avg(det)).all()
+
+
+def test_c_oracle_compiles_without_openmp(tmp_path):
+    """The plain-C oracle is standard C99: it builds with and without OpenMP."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle",
+                       "rqa_oracle.c")
+    for flags in ([], ["-fopenmp"]):
+        out = tmp_path / ("o%d.o" % len(flags))
+        p = subprocess.run([cc, "-std=c99", "-O1", "-Wall", "-Werror", "-c", src, "-o", str(out)] + flags,
+                           capture_output=True, text=True)
+        assert p.returncode == 0, p.stderr
