@@ -59,7 +59,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-cells", type=float, default=1.2e8,
                     help="cells of the oracle's bounded sample")
-    ap.add_argument("--band", type=int, default=0, help="line-pass band width (0 = default)")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="line-pass register window: 8, 16 or 32 diagonals (0 = tuned)")
     ap.add_argument("--select", default="auto", choices=["auto", "radix"],
                     help="auto: learned bracket when a model file exists")
     return ap.parse_args()
@@ -290,8 +291,8 @@ def main():
 
     def make_ctx(schedule, learned=False):
         c = rqa.Context(device=dev, stream=stream, schedule=schedule,
-                        select=rqa.RQA_SELECT_BRACKET if learned else rqa.RQA_SELECT_RADIX,
-                        band=args.band)
+                        select=rqa.RQA_SELECT_AUTO if learned else rqa.RQA_SELECT_RADIX,
+                        tile=args.tile)
         if learned:
             bracket.install(c)
         return c
@@ -306,7 +307,7 @@ def main():
             dist.barrier()
 
     ctx = make_ctx(sched, have_model)
-    tuned_band = rqa.rqa_autotune(ctx, batch, RR, 100)  # keeps --band when one was given
+    tuned_tile = rqa.rqa_autotune(ctx, batch, RR, 100)  # keeps --tile when one was given
     rqa.rqa_set_timing(ctx, True)
     for _ in range(args.warmup):
         step(ctx)
@@ -447,8 +448,8 @@ def main():
             "config": {"workload": args.workload, "desc": workload_desc(args.workload),
                        "form": f"{form} + radix select" if not have_model else f"{form} + learned bracket",
                        "series": S, "cells_per_step": total_cells, "l2": "flushed between steps",
-                       "line_band": tuned_band,
-                       "line_band_from": "--band" if args.band else "rqa_autotune",
+                       "line_tile": tuned_tile,
+                       "line_tile_from": "--tile" if args.tile else "rqa_autotune",
                        "parallelism": f"replicas x{world} (series-independent)"},
             "series_per_s": series_per_s,
             "phase_ms": {n: round(float(v), 4) for n, v in zip(names, phase)},

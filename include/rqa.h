@@ -34,9 +34,12 @@
  *   - A context is not thread safe; use one per host thread.
  *   - K (number of thresholds per series) is 1 .. RQA_K_MAX, so a call can
  *     average over RR = 1..99 % (Sect. 2 considers RR* up to 99).  The line
- *     pass handles up to 31 thresholds per sweep over the cells; a call with
- *     larger K makes ceil(K / 31) sweeps (same results, proportionally
+ *     pass handles up to 20 thresholds per sweep over the cells; a call with
+ *     larger K makes ceil(K / 20) sweeps (same results, proportionally
  *     slower line pass).
+ *   - The line pass (rqa_det_avg, rqa_line_hist, rqa_vline_hist) counts
+ *     series with Ne < 2^26 (6.7e7 vectors, 2.2e15 cells); longer ones are
+ *     RQA_ERR_CAPACITY.
  *   - A series must have Ne >= 2 (P >= 1), otherwise RQA_ERR_TOO_SHORT.
  */
 #ifndef RQA_H
@@ -88,9 +91,11 @@ typedef struct {
     void *stream;      /* cudaStream_t owned by the caller; NULL = default stream */
     int schedule;      /* RQA_SCHED_* */
     int select;        /* RQA_SELECT_* */
-    int band;          /* diagonals per warp band of the line pass: 0 = default
-                          (4), else 4, 8 or 16 (8 and 16 only for (m, tau) =
-                          (1, any), (3, 1), (3, 3); otherwise 4 is used) */
+    int tile;          /* line pass: diagonals whose cells a lane computes from
+                          one register window of the series: 0 = default (16,
+                          or the rqa_autotune choice), else 8, 16 or 32 (8 and
+                          32 only for (m, tau) = (1, any), (3, 1), (3, 3);
+                          otherwise 16 is used) */
     int blocks_per_sm; /* persistent CTAs per SM: 0 = as many as each kernel
                           can keep resident, else at most this many */
     int flags;         /* RQA_FLAG_* */
@@ -144,9 +149,9 @@ const char *rqa_error_string(int code);
 int rqa_abi_version(void);
 
 /* Number of SMs of the context's device and the schedule parameters in use
- * (line-pass band width, blocks per SM as configured: 0 = resident limit);
+ * (line-pass register window, blocks per SM as configured: 0 = resident limit);
  * any pointer may be NULL. */
-int rqa_device_info(rqa_ctx *ctx, int *sm_count, int *band, int *blocks_per_sm);
+int rqa_device_info(rqa_ctx *ctx, int *sm_count, int *tile, int *blocks_per_sm);
 
 /* Per-phase device times of the context's last hot-path call, in ms, when
  * timing is on (rqa_set_timing): [0] finiteness check, [1] coarse counting
@@ -163,12 +168,12 @@ uint64_t rqa_kernel_launches(rqa_ctx *ctx);
 /* Graph replays of rqa_det_avg since the context was created. */
 uint64_t rqa_graph_replays(rqa_ctx *ctx);
 
-/* Line-pass band width tuning: times the line pass over (a prefix of) the
- * batch for each supported band width with the thresholds of rr_num/rr_den,
- * keeps the fastest in the context (used while cfg.band was 0) and returns
- * it in *band (host pointer, may be NULL).  Synchronises the stream. */
+/* Line-pass tuning: times the line pass over (a prefix of) the batch for each
+ * supported register window (cfg.tile) with the thresholds of rr_num/rr_den,
+ * keeps the fastest in the context (used while cfg.tile was 0) and returns
+ * it in *tile (host pointer, may be NULL).  Synchronises the stream. */
 int rqa_autotune(rqa_ctx *ctx, const rqa_batch *batch, const int32_t *rr_num, int32_t rr_den,
-                 int32_t K, int *band);
+                 int32_t K, int *tile);
 
 /* ---- host helpers (no GPU needed) -------------------------------------- */
 
@@ -287,7 +292,7 @@ int rqa_line_measures(rqa_ctx *ctx, const rqa_batch *batch, int32_t K, const uin
  *   vmax         device, S*K uint32, longest vertical line (may be NULL)
  *   vmass        device, S*K uint64, sum of l V_k(l): every recurrent cell of
  *                the matrix, 2 C_k (+ Ne with RQA_FLAG_LOI) (may be NULL)
- * One sweep over every cell of the matrix per group of at most 31 targets
+ * One sweep over every cell of the matrix per group of at most 20 targets
  * (2P + Ne cells: about twice the diagonal line pass).
  */
 int rqa_vline_hist(rqa_ctx *ctx, const rqa_batch *batch, const float *eps, int32_t K,
@@ -349,11 +354,19 @@ int rqa_eps_approx(rqa_ctx *ctx, const rqa_batch *batch, const int32_t *rr_num, 
  *   - status_out: device int (may be NULL) that receives the device-side
  *     status of the call (RQA_OK, RQA_ERR_NONFINITE, ...) when it completes.
  *   - K is at most RQA_NOALLOC_K_MAX here (RQA_ERR_INVALID_ARG above).
+ *   - Series have Ne <= RQA_NOALLOC_NE_MAX vectors here: each work item
+ *     (consecutive diagonals of one series, at most 1024 per series) covers
+ *     at most 2^30 cells so the 32-bit shared counts stay exact; a longer
+ *     series is RQA_ERR_CAPACITY.
+ *   - batch->y, eps_out and the non-NULL count_le, count_lt, status_out must
+ *     be memory the current device can address (its device memory or managed
+ *     memory), else RQA_ERR_INVALID_ARG.
  *   - Returns RQA_ERR_CAPACITY for more than RQA_NOALLOC_MAX_SERIES series,
  *     and the argument errors of rqa_eps_for_rr; nothing is enqueued then.
  */
 #define RQA_NOALLOC_MAX_SERIES 4
 #define RQA_NOALLOC_K_MAX 31
+#define RQA_NOALLOC_NE_MAX 1048576 /* 2^20 vectors per series */
 #define RQA_NOALLOC_SCRATCH_BYTES 1310720 /* 1.25 MiB */
 int rqa_eps_for_rr_noalloc(const rqa_batch *batch, const int32_t *rr_num, int32_t rr_den,
                            int32_t K, float *eps_out, uint64_t *count_le, uint64_t *count_lt,

@@ -69,12 +69,21 @@ int rqa_adam_step(rqa_ctx *ctx, float *params, const float *grads, float *m, flo
 /* Install a trained network in the context (params copied, device pointer)
  * and the widening margin added to both ends of every interval (in ln units).
  * params == NULL removes the model.  With a model, RQA_SELECT_AUTO uses the
- * bracket whenever a call asks for RR = 1..20 % (rr_num 1..20, rr_den 100). */
+ * bracket when a call asks for RR = 1..20 % (rr_num 1..20, rr_den 100), for
+ * the series whose embedding lies in the model's domain (below). */
 int rqa_set_bracket_model(rqa_ctx *ctx, const float *params, float margin);
 
+/* The embeddings (m[i], tau[i]), i < n, the installed network was trained on
+ * (host arrays, copied).  With RQA_SELECT_AUTO only series with one of these
+ * embeddings are bracketed; the others take the full selection, and a call
+ * none of whose series qualifies runs no sketch or network at all.  n = 0
+ * (the default) puts no restriction; RQA_SELECT_BRACKET ignores the domain.
+ * At most 64 pairs; RQA_ERR_INVALID_ARG for m or tau < 1. */
+int rqa_set_bracket_domain(rqa_ctx *ctx, const int32_t *m, const int32_t *tau, int32_t n);
+
 /* Targets of the context's last bracketed selection whose interval held the
- * threshold (hits) and those that needed the full selection (misses); host
- * pointers, synchronises the stream. */
+ * threshold (hits) and those that needed the full selection (misses), over
+ * the series that were bracketed; host pointers, synchronises the stream. */
 int rqa_bracket_stats(rqa_ctx *ctx, uint64_t *hits, uint64_t *misses);
 
 #ifdef __cplusplus

@@ -25,6 +25,7 @@ RQA_SCHED_BATCHED, RQA_SCHED_PER_SERIES = 0, 1
 RQA_SELECT_AUTO, RQA_SELECT_RADIX, RQA_SELECT_BRACKET = 0, 1, 2
 RQA_K_MAX = 127
 RQA_NOALLOC_K_MAX = 31
+RQA_NOALLOC_NE_MAX = 1 << 20
 RQA_LMIN_MAX = 8
 RQA_FEATURES = 131
 RQA_MLP_HIDDEN = 256
@@ -41,7 +42,7 @@ class RqaError(RuntimeError):
 
 class _Config(ctypes.Structure):
     _fields_ = [("device", c_int), ("stream", c_vp), ("schedule", c_int), ("select", c_int),
-                ("band", c_int), ("blocks_per_sm", c_int), ("flags", c_int), ("reserved", c_int * 3)]
+                ("tile", c_int), ("blocks_per_sm", c_int), ("flags", c_int), ("reserved", c_int * 3)]
 
 
 RQA_FLAG_NO_GRAPHS = 1
@@ -91,6 +92,7 @@ _SIGS = {
     "rqa_adam_step": ([c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, c_i32, ctypes.c_float, ctypes.c_float,
                        ctypes.c_float, ctypes.c_float], c_int),
     "rqa_set_bracket_model": ([c_vp, c_vp, ctypes.c_float], c_int),
+    "rqa_set_bracket_domain": ([c_vp, c_vp, c_vp, c_i32], c_int),
     "rqa_bracket_stats": ([c_vp, c_vp, c_vp], c_int),
     "rqa_eps_for_rr_noalloc": ([ctypes.POINTER(_Batch), c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp,
                                 c_vp], c_int),
@@ -200,14 +202,14 @@ class Context:
     """An ``rqa_ctx``: device, stream, schedule and scratch memory."""
 
     def __init__(self, device: int = 0, stream=None, schedule: int = RQA_SCHED_BATCHED,
-                 select: int = RQA_SELECT_AUTO, band: int = 0, blocks_per_sm: int = 0,
+                 select: int = RQA_SELECT_AUTO, tile: int = 0, blocks_per_sm: int = 0,
                  flags: int = 0):
         import torch
         if stream is None:
             stream = torch.cuda.current_stream(device)
         self.stream = stream
         handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-        cfg = _Config(device, c_vp(handle), schedule, select, band, blocks_per_sm, int(flags),
+        cfg = _Config(device, c_vp(handle), schedule, select, tile, blocks_per_sm, int(flags),
                       (c_int * 3)())
         p = c_vp()
         _check(lib().rqa_create(ctypes.byref(p), ctypes.byref(cfg)), "rqa_create")
@@ -231,8 +233,8 @@ class Context:
 
 
 def rqa_create(device: int = 0, stream=None, schedule: int = RQA_SCHED_BATCHED,
-               select: int = RQA_SELECT_AUTO, band: int = 0, blocks_per_sm: int = 0) -> Context:
-    return Context(device, stream, schedule, select, band, blocks_per_sm)
+               select: int = RQA_SELECT_AUTO, tile: int = 0, blocks_per_sm: int = 0) -> Context:
+    return Context(device, stream, schedule, select, tile, blocks_per_sm)
 
 
 def rqa_destroy(ctx: Context):
@@ -244,10 +246,10 @@ def rqa_status(ctx: Context) -> int:
 
 
 def rqa_device_info(ctx: Context):
-    sm, band, bpsm = c_int(), c_int(), c_int()
-    _check(lib().rqa_device_info(ctx.handle, ctypes.byref(sm), ctypes.byref(band),
+    sm, tile, bpsm = c_int(), c_int(), c_int()
+    _check(lib().rqa_device_info(ctx.handle, ctypes.byref(sm), ctypes.byref(tile),
                                  ctypes.byref(bpsm)), "rqa_device_info")
-    return {"sm_count": sm.value, "band": band.value, "blocks_per_sm": bpsm.value}
+    return {"sm_count": sm.value, "tile": tile.value, "blocks_per_sm": bpsm.value}
 
 
 def rqa_target_counts(P: int, rr_num: Sequence[int], rr_den: int) -> np.ndarray:
@@ -380,13 +382,13 @@ def rqa_graph_replays(ctx: Context) -> int:
 
 
 def rqa_autotune(ctx: Context, batch: Batch, rr_num, rr_den: int) -> int:
-    """Pick the fastest line-pass band width for this batch; returns it."""
+    """Pick the fastest line-pass register window for this batch; returns it."""
     rr = np.ascontiguousarray(rr_num, dtype=np.int32)
     b = batch._c()
-    band = c_int()
+    tile = c_int()
     _check(lib().rqa_autotune(ctx.handle, ctypes.byref(b), _np_ptr(rr), int(rr_den), len(rr),
-                              ctypes.byref(band)), "rqa_autotune")
-    return band.value
+                              ctypes.byref(tile)), "rqa_autotune")
+    return tile.value
 
 
 def rqa_line_hist(ctx: Context, batch: Batch, eps, K: int, hist=None, hist_offsets=None,
@@ -455,6 +457,16 @@ def rqa_set_bracket_model(ctx: Context, params, margin: float = 0.0):
     _check(lib().rqa_set_bracket_model(ctx.handle,
                                        _dev_ptr(params, torch.float32, RQA_MLP_PARAMS, "params"),
                                        float(margin)), "rqa_set_bracket_model")
+
+
+def rqa_set_bracket_domain(ctx: Context, pairs):
+    """The (m, tau) embeddings the installed network was trained on; [] = any."""
+    pairs = list(pairs)
+    m = np.ascontiguousarray([p[0] for p in pairs], dtype=np.int32)
+    tau = np.ascontiguousarray([p[1] for p in pairs], dtype=np.int32)
+    _check(lib().rqa_set_bracket_domain(ctx.handle, _np_ptr(m) if pairs else None,
+                                        _np_ptr(tau) if pairs else None, len(pairs)),
+           "rqa_set_bracket_domain")
 
 
 def rqa_bracket_stats(ctx: Context):

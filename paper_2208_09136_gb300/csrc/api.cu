@@ -53,8 +53,8 @@ struct rqa_ctx {
     int schedule = RQA_SCHED_BATCHED;
     int select = RQA_SELECT_AUTO;
     int band = 16;          // diagonals per band of the counting rounds
-    int band_lines = 0;     // ... of the line pass (0 = tuned default)
-    bool band_fixed = false;  // the caller chose the band: rqa_autotune keeps it
+    int line_tile = 0;      // diagonals per register window of the line pass (0 = default)
+    bool tile_fixed = false;  // the caller chose the tile: rqa_autotune keeps it
     bool loi = false;         // RQA_FLAG_LOI: rates and DET over the whole matrix
     int bpsm = 0;
     int sm_count = 0;
@@ -71,6 +71,7 @@ struct rqa_ctx {
     // learned bracket
     DevBuf mlp;                 // installed network parameters
     bool has_model = false;
+    std::vector<int32_t> dom_m, dom_tau;  // embeddings the network was trained on (empty: any)
     float margin = 0.f;
     DevBuf feats, centre, ymlp, acts, bstats, learn_scratch;
     uint64_t sketch_seed = 1;
@@ -112,10 +113,13 @@ struct Plan {
     std::vector<int32_t> order;              // series by size, largest first
     std::vector<int64_t> uprefix;            // S+1 unit-count prefix along order
     int32_t chunk = 1;                       // bands per line-pass unit (batched)
-    int32_t band_lines = DL_DEFAULT;         // diagonals per band of the line pass
+    int32_t line_tile = LINE_TILE_DEFAULT;   // diagonals per register window of the line pass
+    int32_t ne_max = 0;                      // largest Ne of the batch
     std::vector<int32_t> ident;              // 0..S-1
     std::vector<int64_t> uprefix1;           // [2s], [2s+1] = 0, units of s alone
     std::vector<int32_t> chunk1;             // bands per unit of s alone
+    std::vector<uint8_t> dom;                // 1: the series may be bracketed
+    bool any_dom = false;
     // device pointers into the arena after upload
     SeriesDev *d_sd = nullptr;
     uint64_t *d_T = nullptr;
@@ -125,6 +129,7 @@ struct Plan {
     int64_t *d_uprefix = nullptr, *d_uprefix1 = nullptr;
     int32_t *d_lmin = nullptr;
     int64_t *d_hoff = nullptr;
+    uint8_t *d_dom = nullptr;
 };
 
 int check_cuda(cudaError_t e)
@@ -242,6 +247,18 @@ int make_plan(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_
         total_cells += d.P;
     }
     pl.total = b->offsets[S];
+    // series the learned bracket may take: any when the bracket is forced or
+    // the network's domain is unrestricted, else those with a trained embedding
+    pl.dom.assign(S, 1);
+    if (c->select != RQA_SELECT_BRACKET && !c->dom_m.empty())
+        for (int s = 0; s < S; ++s) {
+            bool in = false;
+            for (size_t i = 0; i < c->dom_m.size() && !in; ++i)
+                in = c->dom_m[i] == b->m[s] && c->dom_tau[i] == b->tau[s];
+            pl.dom[s] = in ? 1 : 0;
+        }
+    pl.any_dom = false;
+    for (int s = 0; s < S; ++s) pl.any_dom |= pl.dom[s] != 0;
     pl.mt = E_GENERIC;
     if (uniform && m0 <= 4) pl.mt = m0;
     if (uniform && m0 == 1) pl.mt = E_M1T1;  // tau plays no part when m = 1
@@ -281,16 +298,21 @@ int make_plan(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_
         build_items(pl.sd[s], s, c->band, t, 4 * WARPS, pl.items_ser, nullptr);
         pl.ser_begin[s + 1] = (int)pl.items_ser.size();
     }
-    // warp work units (line pass): runs of `chunk` bands, series largest
-    // first; about eight units per warp so the tail stays short while each
-    // unit's histogram flush is spread over many cells
-    const int64_t n_warps = (int64_t)c->sm_count * 3 * WARPS;  // resident warps of the line pass
+    // warp work units (line pass): runs of `chunk` bands of LINE_BAND
+    // diagonals, series largest first; about eight units per warp so the tail
+    // stays short while each unit's histogram flush is spread over many cells.
+    // A unit covers at most 2^33 cells, so the warp's 32-bit counts of lines of
+    // length >= 4 (each line and the cell after it: >= 5 cells) stay exact.
+    const int64_t n_warps = (int64_t)c->sm_count * 16;  // resident warps of the line pass
+    for (int s = 0; s < S; ++s) pl.ne_max = std::max(pl.ne_max, pl.sd[s].ne);
+    const int64_t chunk_cap = std::max<int64_t>(1, ((int64_t)1 << 28) / std::max(pl.ne_max, 1));
     auto chunk_for = [&](int64_t bands) {
-        return (int32_t)std::max<int64_t>(4, std::min<int64_t>(64, bands / (n_warps * 8)));
+        const int64_t ch = std::max<int64_t>(1, std::min<int64_t>(64, bands / (n_warps * 8)));
+        return (int32_t)std::min(ch, chunk_cap);
     };
-    pl.band_lines = c->band_lines ? c->band_lines : DL_DEFAULT;
-    if (!lines_band_ok(pl.mt, pl.band_lines)) pl.band_lines = DL_DEFAULT;
-    auto nbl = [&](int s) { return (int64_t)(pl.sd[s].ne - 1 + pl.band_lines - 1) / pl.band_lines; };
+    pl.line_tile = c->line_tile ? c->line_tile : LINE_TILE_DEFAULT;
+    if (!lines_tile_ok(pl.mt, pl.line_tile)) pl.line_tile = LINE_TILE_DEFAULT;
+    auto nbl = [&](int s) { return (int64_t)(pl.sd[s].ne - 1 + LINE_BAND - 1) / LINE_BAND; };
     int64_t total_bands = 0;
     for (int s = 0; s < S; ++s) total_bands += nbl(s);
     pl.chunk = chunk_for(total_bands);
@@ -326,7 +348,8 @@ int upload_plan(rqa_ctx *c, Plan &pl, const int32_t *lmin, int n_lmin, const int
     const size_t o_upre1 = align16(o_ident + pl.ident.size() * sizeof(int32_t));
     const size_t o_lmin = align16(o_upre1 + pl.uprefix1.size() * sizeof(int64_t));
     const size_t o_hoff = align16(o_lmin + (size_t)n_lmin * sizeof(int32_t));
-    const size_t total = align16(o_hoff + (hoff ? (size_t)(pl.S + 1) * sizeof(int64_t) : 0));
+    const size_t o_dom = align16(o_hoff + (hoff ? (size_t)(pl.S + 1) * sizeof(int64_t) : 0));
+    const size_t total = align16(o_dom + pl.dom.size());
 
     if (c->stage_pending) {
         if (cudaEventSynchronize(c->stage_done) != cudaSuccess) return check_cuda(cudaGetLastError());
@@ -355,6 +378,7 @@ int upload_plan(rqa_ctx *c, Plan &pl, const int32_t *lmin, int n_lmin, const int
     std::memcpy(h + o_upre1, pl.uprefix1.data(), pl.uprefix1.size() * sizeof(int64_t));
     if (n_lmin) std::memcpy(h + o_lmin, lmin, (size_t)n_lmin * sizeof(int32_t));
     if (hoff) std::memcpy(h + o_hoff, hoff, (size_t)(pl.S + 1) * sizeof(int64_t));
+    std::memcpy(h + o_dom, pl.dom.data(), pl.dom.size());
     char *d = static_cast<char *>(c->arena.p);
     if (int rc = check_cuda(cudaMemcpyAsync(d, h, total, cudaMemcpyHostToDevice, c->stream))) return rc;
     if (int rc = check_cuda(cudaEventRecord(c->stage_done, c->stream))) return rc;
@@ -369,6 +393,7 @@ int upload_plan(rqa_ctx *c, Plan &pl, const int32_t *lmin, int n_lmin, const int
     pl.d_uprefix1 = reinterpret_cast<int64_t *>(d + o_upre1);
     pl.d_lmin = reinterpret_cast<int32_t *>(d + o_lmin);
     pl.d_hoff = reinterpret_cast<int64_t *>(d + o_hoff);
+    pl.d_dom = reinterpret_cast<uint8_t *>(d + o_dom);
     return RQA_OK;
 }
 
@@ -466,7 +491,7 @@ int run_select(rqa_ctx *c, const Plan &pl, const SelBufs &sb, const Item *items,
                                             c->stream)))
             return rc;
         c->launches += 3;
-        if (int rc = launched(c, launch_bracket(ym, centre, c->margin, ns, K,
+        if (int rc = launched(c, launch_bracket(ym, centre, c->margin, ns, K, pl.d_dom + s0,
                                                 sb.tab_sub + (int64_t)s0 * NCOARSE, sb.n_sub + s0,
                                                 sb.range + 2 * (int64_t)s0, c->stream)))
             return rc;
@@ -492,7 +517,7 @@ int run_select(rqa_ctx *c, const Plan &pl, const SelBufs &sb, const Item *items,
                                                P<int>(c->status), c->stream)))
             return rc;
         if (r == 0)
-            if (int rc = launched(c, launch_bracket_stats(sb.level + (int64_t)s0 * K, (int64_t)ns * K,
+            if (int rc = launched(c, launch_bracket_stats(sb.level + (int64_t)s0 * K, pl.d_dom + s0, ns, K,
                                                           P<unsigned long long>(c->bstats), c->stream)))
                 return rc;
         if (r >= 1) mark(c, 1 + r);
@@ -581,7 +606,7 @@ int run_lines(rqa_ctx *c, const Plan &pl, const float *eps, uint64_t *hist, cons
     a.y = pl.y;
     a.series = pl.d_sd;
     a.band = c->band;
-    a.band_lines = pl.band_lines;
+    a.line_tile = pl.line_tile;
     a.status = P<int>(c->status);
     unsigned *q = nullptr;
     const int full_grid = persistent_grid(c, (size_t)1 << 30);
@@ -749,7 +774,7 @@ int rqa_create(rqa_ctx **out, const rqa_config *cfg)
     if (cfg->schedule != RQA_SCHED_BATCHED && cfg->schedule != RQA_SCHED_PER_SERIES)
         return RQA_ERR_INVALID_ARG;
     if (cfg->select < RQA_SELECT_AUTO || cfg->select > RQA_SELECT_BRACKET) return RQA_ERR_INVALID_ARG;
-    if (cfg->band != 0 && cfg->band != 4 && cfg->band != 8 && cfg->band != 16)
+    if (cfg->tile != 0 && cfg->tile != 8 && cfg->tile != 16 && cfg->tile != 32)
         return RQA_ERR_INVALID_ARG;
     if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 8) return RQA_ERR_INVALID_ARG;
     int ndev = 0;
@@ -765,8 +790,8 @@ int rqa_create(rqa_ctx **out, const rqa_config *cfg)
     c->schedule = cfg->schedule;
     c->select = cfg->select;
     c->band = BAND;
-    c->band_lines = cfg->band;
-    c->band_fixed = cfg->band != 0;
+    c->line_tile = cfg->tile;
+    c->tile_fixed = cfg->tile != 0;
     c->graphs = !(cfg->flags & RQA_FLAG_NO_GRAPHS);
     c->loi = (cfg->flags & RQA_FLAG_LOI) != 0;
     c->bpsm = cfg->blocks_per_sm;
@@ -823,11 +848,11 @@ int rqa_status(rqa_ctx *c)
     return st;
 }
 
-int rqa_device_info(rqa_ctx *c, int *sm_count, int *band, int *blocks_per_sm)
+int rqa_device_info(rqa_ctx *c, int *sm_count, int *tile, int *blocks_per_sm)
 {
     if (!c) return RQA_ERR_INVALID_ARG;
     if (sm_count) *sm_count = c->sm_count;
-    if (band) *band = c->band_lines ? c->band_lines : DL_DEFAULT;
+    if (tile) *tile = c->line_tile ? c->line_tile : LINE_TILE_DEFAULT;
     if (blocks_per_sm) *blocks_per_sm = c->bpsm;  // 0: as many as each kernel keeps resident
     return RQA_OK;
 }
@@ -843,6 +868,7 @@ int rqa_eps_for_rr(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_
     cudaSetDevice(c->device);
     Plan pl;
     if (int rc = make_plan(c, b, rr_num, rr_den, K, pl)) return rc;
+    bracket = bracket && pl.any_dom;
     if (int rc = ensure_select_bufs(c, pl.S, K)) return rc;
     if (int rc = upload_plan(c, pl, nullptr, 0, nullptr)) return rc;
     return select_all(c, b, pl, eps_out, count_le, count_lt, bracket);
@@ -867,6 +893,8 @@ int rqa_det_avg(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t r
     cudaSetDevice(c->device);
     Plan pl;
     if (int rc = make_plan(c, b, eps ? nullptr : rr_num, rr_den, K, pl)) return rc;
+    if (pl.ne_max > LINE_NE_MAX) return RQA_ERR_CAPACITY;
+    bracket = bracket && pl.any_dom;
     // every scratch buffer sized before anything is enqueued (and captured)
     if (int rc = ensure_line_bufs(c, pl.S, K)) return rc;
     if (!eps)
@@ -885,7 +913,8 @@ int rqa_det_avg(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t r
         auto put = [&](uint64_t v) { sig.push_back(v); };
         auto ptr = [&](const void *p) { put((uint64_t)(uintptr_t)p); };
         put((uint64_t)pl.S); put((uint64_t)K); put((uint64_t)n_lmin); put((uint64_t)rr_den);
-        put(bracket); put((uint64_t)c->schedule); put((uint64_t)pl.band_lines); put(c->timing);
+        put(bracket); put((uint64_t)c->schedule); put((uint64_t)pl.line_tile); put(c->timing);
+        for (int s = 0; s < pl.S; ++s) put(pl.dom[s]);
         put(c->loi);
         uint32_t mb;
         std::memcpy(&mb, &c->margin, 4);
@@ -975,6 +1004,7 @@ int rqa_line_hist(rqa_ctx *c, const rqa_batch *b, const float *eps, int32_t K, u
     cudaSetDevice(c->device);
     Plan pl;
     if (int rc = make_plan(c, b, nullptr, 0, K, pl)) return rc;
+    if (pl.ne_max > LINE_NE_MAX) return RQA_ERR_CAPACITY;
     if (int rc = ensure_line_bufs(c, pl.S, K)) return rc;
     if (int rc = upload_plan(c, pl, nullptr, 0, hist ? hist_offsets : nullptr)) return rc;
     mark(c, 0);
@@ -1022,13 +1052,14 @@ int rqa_vline_hist(rqa_ctx *c, const rqa_batch *b, const float *eps, int32_t K, 
     if (int rc = validate_batch(b)) return rc;
     if (int rc = validate_hist(b, K, vhist, vhist_offsets, c->loi ? 1 : 0)) return rc;
     cudaSetDevice(c->device);
-    // the vertical pass walks bands of DL_DEFAULT columns: a plan for that width
-    const int saved = c->band_lines;
-    c->band_lines = DL_DEFAULT;
+    // the vertical pass runs the default register window
+    const int saved = c->line_tile;
+    c->line_tile = LINE_TILE_DEFAULT;
     Plan pl;
     const int rcp = make_plan(c, b, nullptr, 0, K, pl);
-    c->band_lines = saved;
+    c->line_tile = saved;
     if (rcp) return rcp;
+    if (pl.ne_max > LINE_NE_MAX) return RQA_ERR_CAPACITY;
     if (int rc = ensure_line_bufs(c, pl.S, K)) return rc;
     if (int rc = upload_plan(c, pl, nullptr, 0, vhist ? vhist_offsets : nullptr)) return rc;
     if (int rc = launched(c, launch_check_finite(b->y, pl.total, P<int>(c->status), c->stream)))
@@ -1154,8 +1185,8 @@ int rqa_autotune(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t 
     if (!c) return RQA_ERR_INVALID_ARG;
     if (int rc = validate_batch(b)) return rc;
     if (int rc = validate_rr(rr_num, rr_den, K)) return rc;
-    if (c->band_fixed) {
-        if (band) *band = c->band_lines;
+    if (c->tile_fixed) {
+        if (band) *band = c->line_tile;
         return RQA_OK;
     }
     cudaSetDevice(c->device);
@@ -1182,13 +1213,13 @@ int rqa_autotune(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t 
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return check_cuda(cudaGetLastError());
-    const int saved_band = c->band_lines;
-    int best = DL_DEFAULT;
+    const int saved_band = c->line_tile;
+    int best = LINE_TILE_DEFAULT;
     float best_ms = 3.4e38f;
-    const int cand[3] = {4, 8, 16};
+    const int cand[3] = {8, 16, 32};
     for (int ci = 0; ci < 3 && rc == RQA_OK; ++ci) {
-        if (!lines_band_ok(probe.mt, cand[ci])) continue;
-        c->band_lines = cand[ci];
+        if (!lines_tile_ok(probe.mt, cand[ci])) continue;
+        c->line_tile = cand[ci];
         float t_min = 3.4e38f;
         for (int rep = 0; rep < 2 && rc == RQA_OK; ++rep) {
             cudaEventRecord(e0, c->stream);
@@ -1205,8 +1236,8 @@ int rqa_autotune(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t 
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->band_lines = rc == RQA_OK ? best : saved_band;
-    if (band) *band = c->band_lines;
+    c->line_tile = rc == RQA_OK ? best : saved_band;
+    if (band) *band = c->line_tile;
     return rc;
 }
 
@@ -1271,6 +1302,16 @@ int rqa_set_bracket_model(rqa_ctx *c, const float *params, float margin)
         return rc;
     c->has_model = true;
     c->margin = margin;
+    return RQA_OK;
+}
+
+int rqa_set_bracket_domain(rqa_ctx *c, const int32_t *m, const int32_t *tau, int32_t n)
+{
+    if (!c || n < 0 || n > 64 || (n > 0 && (!m || !tau))) return RQA_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (m[i] < 1 || tau[i] < 1) return RQA_ERR_INVALID_ARG;
+    c->dom_m.assign(m, m + n);
+    c->dom_tau.assign(tau, tau + n);
     return RQA_OK;
 }
 

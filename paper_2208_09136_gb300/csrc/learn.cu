@@ -283,11 +283,22 @@ cudaError_t adam_step(float *p, const float *g, float *m, float *v, int64_t n, i
 // between split buckets.  Keys between the first and the last split bucket
 // are counted either way (unsplit buckets at coarse resolution).
 __global__ void k_bracket(const float *__restrict__ Yb, const float *__restrict__ centre,
-                          float margin, int K, int8_t *tab_sub, int32_t *n_sub, uint32_t *range)
+                          float margin, int K, const uint8_t *__restrict__ dom, int8_t *tab_sub,
+                          int32_t *n_sub, uint32_t *range)
 {
     __shared__ uint16_t lo_b[KMAX], hi_b[KMAX], mid_b[KMAX];
     __shared__ int8_t tb[NCOARSE];
     const int s = blockIdx.x;
+    if (!dom[s]) {  // outside the network's domain: the full selection takes it
+        int8_t *tab = tab_sub + (int64_t)s * NCOARSE;
+        for (int x = threadIdx.x; x < NCOARSE; x += blockDim.x) tab[x] = -1;
+        if (threadIdx.x == 0) {
+            n_sub[s] = 0;
+            range[2 * s] = 0xffffffffu;
+            range[2 * s + 1] = 0u;
+        }
+        return;
+    }
     for (int x = threadIdx.x; x < NCOARSE; x += blockDim.x) tb[x] = -1;
     if (threadIdx.x < K) {
         const float c = centre[s];
@@ -385,19 +396,25 @@ __global__ void k_bracket(const float *__restrict__ Yb, const float *__restrict_
 }
 
 cudaError_t launch_bracket(const float *Y, const float *centre, float margin, int S, int K,
-                           int8_t *tab_sub, int32_t *n_sub, uint32_t *range, cudaStream_t st)
+                           const uint8_t *dom, int8_t *tab_sub, int32_t *n_sub, uint32_t *range,
+                           cudaStream_t st)
 {
-    k_bracket<<<S, 256, 0, st>>>(Y, centre, margin, K, tab_sub, n_sub, range);
+    if (!dom) return cudaErrorInvalidValue;
+    k_bracket<<<S, 256, 0, st>>>(Y, centre, margin, K, dom, tab_sub, n_sub, range);
     return cudaGetLastError();
 }
 
 // Hits and misses of a bracketed selection: a target hit when its key
-// prefix was fixed by the split round (level 2 right after it).
-__global__ void k_bracket_stats(const uint8_t *level, int64_t n, unsigned long long *hm)
+// prefix was fixed by the split round (level 2 right after it); series
+// outside the network's domain (dom[s] == 0) are not counted.
+__global__ void k_bracket_stats(const uint8_t *level, const uint8_t *dom, int S, int K,
+                                unsigned long long *hm)
 {
     unsigned long long h = 0, m = 0;
+    const int64_t n = (int64_t)S * K;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
+        if (!dom[e / K]) continue;
         if (level[e] == 2) ++h;
         else ++m;
     }
@@ -405,10 +422,12 @@ __global__ void k_bracket_stats(const uint8_t *level, int64_t n, unsigned long l
     atomicAdd(hm + 1, m);
 }
 
-cudaError_t launch_bracket_stats(const uint8_t *level, int64_t n, unsigned long long *hm,
-                                 cudaStream_t st)
+cudaError_t launch_bracket_stats(const uint8_t *level, const uint8_t *dom, int S, int K,
+                                 unsigned long long *hm, cudaStream_t st)
 {
-    k_bracket_stats<<<(int)std::min<int64_t>((n + 255) / 256, 256), 256, 0, st>>>(level, n, hm);
+    if (!dom || S < 1 || K < 1) return cudaErrorInvalidValue;
+    const int64_t n = (int64_t)S * K;
+    k_bracket_stats<<<(int)std::min<int64_t>((n + 255) / 256, 256), 256, 0, st>>>(level, dom, S, K, hm);
     return cudaGetLastError();
 }
 

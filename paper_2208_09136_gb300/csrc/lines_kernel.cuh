@@ -1,0 +1,548 @@
+// The line pass kernel (template).  Diagonal lines of the never-materialised recurrence matrices for all K
+// thresholds at once (Eq. 4; Sect. 4: upper triangle, cells computed on the
+// fly, line lengths from the beginnings and ends of runs).
+//
+// A warp owns a band of LD = 32 consecutive diagonals and walks down it 32
+// rows at a time.  Each 32 x 32 row block takes two phases:
+//
+//  cells  lane t holds row i0+t.  For every diagonal j of the band it computes
+//         the distance of cell (i0+t, i0+t+d_lo+j) and its rank
+//         r = #{k : eps_k < d} (one lookup in a bucket table of the
+//         thresholds, or a 5-step search over them); five __ballot_sync calls
+//         publish the bit planes of r over the 32 rows, and one lane stores
+//         them in shared memory.
+//  runs   lane j holds diagonal j.  It reads its five planes and, for every
+//         threshold k, rebuilds the 32-row recurrence word {t : r_t <= k} (the
+//         borrow out of r - (k+1), two LOP3s).  A line ends at row t-1 where
+//         row t-1 is recurrent and row t is not; copies of the word shifted
+//         down by 1..4 rows (the rows above the block come from the state
+//         carried from the previous block) tell whether that line is at least
+//         2, 3 or 4 long, so lines of length 1, 2 and 3 are counted with three
+//         popcounts per word.  Lines of length >= 4 are measured one by one
+//         from the nearest non-recurrent row above their end, or from the
+//         carried run length when the run started in an earlier block.
+//
+// All K thresholds share one distance evaluation per cell, and every lane
+// works on its own diagonal in the run phase.  The run state carried from one
+// row block to the next (per lane and threshold) is the top four bits of the
+// previous word and the length of the run open at its last row.
+//
+// Outputs per (series, threshold): P_k(l) (lengths 1..3 as packed register
+// tallies, 4..WSH in the warp's shared histogram, both flushed once per work
+// unit; WSH+1..LSH in the series' global short histogram; longer lines to the
+// caller's full histogram), L_max, and C_k = sum of l P_k(l), the recurrent
+// cells.
+//
+// The vertical pass (VERT) is the same kernel over bands of 32 consecutive
+// columns walked over every row of the matrix: the word of column c is the
+// ballot over 32 consecutive rows, so its runs are vertical lines.
+#pragma once
+#include <cstdint>
+#include <type_traits>
+#include "rqa_common.cuh"
+
+namespace rqa {
+
+constexpr int LD = 32;        // diagonals (or columns) per band: one per lane in the run phase
+constexpr int KT = LINE_KMAX; // thresholds per sweep: per-lane carry state and tallies in registers
+constexpr int WSH = 44;       // lines of length 4..WSH counted in the warp's shared histogram
+constexpr int HROW = WSH + 1; // lengths 0..WSH of that histogram (row 0 unused)
+constexpr int TMAX = 384;     // entries of the rank table
+constexpr uint32_t CMASK = 0x0FFFFFFFu;  // carry state: length of the open run ...
+constexpr uint32_t TOP4 = 0xF0000000u;   // ... and the top four rows of the previous word
+constexpr int SETTLE = 60;    // row blocks between tally settles (10-bit fields, <= 17 per block)
+
+static_assert(LSH > WSH, "lengths WSH+1..LSH go to the global short histogram");
+
+// Per-warp shared memory, in 32-bit words:
+//   lq    [KT][LD] 8 bytes each: when the word of threshold k of diagonal j
+//         ends lines of length >= 4, their end mask and the run open above
+//         the word; they are measured after the threshold loop (the word
+//         itself is rebuilt there from the row block's planes)
+//   pl    [LD][4] bit planes 0..3 of the ranks of the current row block (16-byte rows)
+//   pl4   [LD]    bit plane 4
+//   epsb  [32]    threshold keys of the current series (padding above every key)
+//   tab   [TMAX]  rank table
+//   hs    [HROW][32] line counts by length, column k for threshold k (a lane
+//         owns a bank): lengths 1..3 from the tallies, 4..WSH one by one
+constexpr int O_LQ = 0, O_PL = O_LQ + KT * LD * 2, O_PL4 = O_PL + LD * 4, O_EPS = O_PL4 + LD,
+              O_TAB = O_EPS + 32, O_HS = O_TAB + TMAX, WARP_WORDS = (O_HS + HROW * 32 + 3) & ~3;
+
+// CTAs of 2 warps: eight fit per SM (shared memory and registers), sixteen warps
+constexpr int LTHREADS = 64;
+constexpr int LWARPS = LTHREADS / 32;
+inline int lines_smem_bytes_impl() { return LWARPS * WARP_WORDS * 4; }
+
+// Recurrence word of threshold k over the 32 rows: bit t = [r_t <= k], i.e.
+// the borrow out of r_t - (k+1) rippled through the bit planes B[0..4] of the
+// ranks.  k is a compile-time constant after unrolling, so every step is a
+// two-input function of (plane, borrow) and the compiler fuses pairs of steps
+// into single LOP3s.  Rank 31 (a cell outside the matrix) is recurrent for no
+// k <= 30.
+__device__ __forceinline__ uint32_t rank_le_word(const uint32_t (&B)[5], int k)
+{
+    const int c = k + 1;
+    uint32_t lt = 0;
+    bool on = false;
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+        const bool cb = (c >> b) & 1;
+        if (!on) {
+            if (cb) {
+                lt = ~B[b];
+                on = true;
+            }
+        } else {
+            lt = cb ? (~B[b] | lt) : (~B[b] & lt);
+        }
+    }
+    return lt;
+}
+
+// 3-input bitwise function with an 8-bit truth table (one LOP3 instruction):
+// bit i of the table is the output for (a, b, c) = bits of (0xF0, 0xCC, 0xAA).
+template <uint32_t LUT>
+__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+    return d;
+}
+
+// The same word for a threshold that differs between lanes: kbm[b] is all
+// ones where bit b of k + 1 is set.  Each step is the borrow of one bit
+// plane: (~r & c) | (~r & borrow) | (c & borrow), one LOP3.
+__device__ __forceinline__ uint32_t rank_le_word_lane(uint32_t b0, uint32_t b1, uint32_t b2,
+                                                      uint32_t b3, uint32_t b4,
+                                                      const uint32_t (&kbm)[5])
+{
+    uint32_t w = lop3<0x0C>(b0, kbm[0], 0u);  // ~r0 & c0
+    w = lop3<0x8E>(b1, kbm[1], w);
+    w = lop3<0x8E>(b2, kbm[2], w);
+    w = lop3<0x8E>(b3, kbm[3], w);
+    return lop3<0x8E>(b4, kbm[4], w);
+}
+
+// Series s and bands [b_lo, b_hi) of work unit u: a unit is a.chunk
+// consecutive bands of one series; units run over the series in a.order
+// (largest first), band 0 (longest diagonals) first.  The vertical pass uses
+// the same units over bands of columns; a series has ceil(Ne / LD) of them,
+// at most one more than of diagonals, which its last unit takes on.
+template <bool VERT>
+__device__ __forceinline__ void unit_of(const CellArgs &a, int64_t u, int &s, int &b_lo,
+                                        int &b_hi, const SeriesDev *series)
+{
+    int lo = 0, hi = a.n_pos;  // last pos with uprefix[pos] <= u
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (a.uprefix[mid] <= u) lo = mid;
+        else hi = mid;
+    }
+    s = a.order[lo];
+    b_lo = (int)(u - a.uprefix[lo]) * a.chunk;
+    const int nbd = (series[s].ne - 1 + LD - 1) / LD;
+    b_hi = min(b_lo + a.chunk, nbd);
+    if (VERT && b_lo + a.chunk >= nbd) b_hi = (series[s].ne + LD - 1) / LD;
+}
+
+// Warp-centric: every warp pulls units from one global queue and keeps its
+// own histogram in shared memory, flushed after each unit.  No CTA-wide
+// barrier, so no warp waits for another.
+// JC: diagonals whose cells a lane computes from one register window of the
+// series (the cell phase walks the band's 32 diagonals in LD / JC windows).
+// Transpose a 32 x 32 bit matrix held one row per lane: on return lane k
+// holds column k (bit j of the result = bit k of lane j's word).  Five rounds
+// of exchanging off-diagonal blocks with the lane s apart.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane)
+{
+    constexpr uint32_t MASKS[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        const int sh = 16 >> r;
+        const uint32_t m = MASKS[r];
+        const uint32_t y = __shfl_xor_sync(FULL, x, sh);
+        x = (lane & sh) ? ((x & ~m) | ((y & ~m) >> sh)) : ((x & m) | ((y & m) << sh));
+    }
+    return x;
+}
+
+template <int M, int TAU, int JC, bool VERT>
+__global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, int K)
+{
+    static_assert(LD % JC == 0 && JC % 4 == 0, "windows of whole plane-4 groups");
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *ws = reinterpret_cast<uint32_t *>(smem) + warp * WARP_WORDS;
+    uint32_t *pl = ws + O_PL, *pl4 = ws + O_PL4, *epsb = ws + O_EPS, *tab = ws + O_TAB;
+    uint32_t *hs = ws + O_HS + lane;  // this lane's column: [l * 32], threshold k = lane
+    uint2 *lqa = reinterpret_cast<uint2 *>(ws + O_LQ);  // [k * LD + j]
+    uint2 *lq = lqa + lane;                               // slots of this lane's diagonal
+    // lane k: the bits of k + 1 as masks, for its own recurrence words
+    uint32_t kbm[5];
+#pragma unroll
+    for (int b = 0; b < 5; ++b) kbm[b] = (((lane + 1) >> b) & 1) ? FULL : 0u;
+    const bool klane = lane < K;
+
+    for (int l = 0; l < HROW; ++l) hs[l * 32] = 0;
+    __syncwarp();
+    uint64_t lmass = 0;  // lane k: cells on lines of threshold k longer than WSH (this unit)
+    uint32_t lmx = 0;    // lane k: the longest of them
+
+    int cur = -1;
+    bool bad = false;
+    SeriesDev sd{};
+    int tshift = 0, tbm1 = 0, tnb = 0;
+    uint32_t tmul = 0;  // 2^(32 - tshift)
+    bool use_tab = false;
+    uint32_t tal[KT];   // per threshold: ends of lines >= 1, >= 2, >= 3 minus those >= 4
+                        // (10-bit fields at bits 0, 10, 20)
+#pragma unroll
+    for (int k = 0; k < KT; ++k) tal[k] = 0;
+    int nrb = 0;        // row blocks since the last settle
+
+    // tallies -> column k, rows 1..3: P(1) = f1 - f2, P(2) = f2 - f3, P(3) = f3
+    auto settle = [&]() {
+        uint32_t g1 = 0, g2 = 0, g3 = 0;  // lane k: the sums of threshold k
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            if (k < K) {
+                const uint32_t f1 = __reduce_add_sync(FULL, tal[k] & 1023u);
+                const uint32_t f2 = __reduce_add_sync(FULL, (tal[k] >> 10) & 1023u);
+                const uint32_t f3 = __reduce_add_sync(FULL, tal[k] >> 20);
+                if (lane == k) {
+                    g1 = f1;
+                    g2 = f2;
+                    g3 = f3;
+                }
+            }
+            tal[k] = 0;
+        }
+        if (klane) {
+            hs[1 * 32] += g1 - g2;
+            hs[2 * 32] += g2 - g3;
+            hs[3 * 32] += g3;
+        }
+        nrb = 0;
+        __syncwarp();
+    };
+
+    // lane k: column k to the series' short histogram; C_k is the line mass,
+    // sum over l of l * P_k(l) (every recurrent cell lies on exactly one line
+    // of its diagonal), and L_max the longest line
+    auto flush = [&]() {
+        if (cur < 0) return;
+        settle();
+        if (klane) {
+            const int64_t o = (int64_t)cur * lb.kstride + lb.k0 + lane;
+            uint64_t *gs = lb.hshort + o * LSH;
+            uint64_t cnt = lmass;
+            uint32_t lm = lmx;
+#pragma unroll 1
+            for (int l = 1; l <= WSH; ++l) {  // row l: one bank per lane
+                const uint32_t v = hs[l * 32];
+                if (v) {
+                    atomicAdd(reinterpret_cast<unsigned long long *>(gs + (l - 1)),
+                              (unsigned long long)v);
+                    hs[l * 32] = 0;
+                    cnt += (uint64_t)l * v;
+                    lm = max(lm, (uint32_t)l);
+                }
+            }
+            if (cnt) atomicAdd(reinterpret_cast<unsigned long long *>(lb.count + o),
+                               (unsigned long long)cnt);
+            if (lm) atomicMax(lb.lmax + o, lm);
+        }
+        lmass = 0;
+        lmx = 0;
+        __syncwarp();
+    };
+
+    for (;;) {
+        int64_t u = 0;
+        if (lane == 0) u = (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(a.queue), 1ull);
+        u = __shfl_sync(FULL, u, 0);
+        if (u >= a.n_units) break;
+        int s, ub_lo, ub_hi;
+        unit_of<VERT>(a, u, s, ub_lo, ub_hi, a.series);
+        if (s != cur) {
+            flush();
+            cur = s;
+            sd = a.series[s];
+            uint32_t v = 0xffffffffu;   // padding: above every key
+            bool ok = true;
+            if (klane) {
+                v = __float_as_uint(lb.eps[(int64_t)s * lb.kstride + lb.k0 + lane]);
+                if (v == 0x80000000u) v = 0u;                           // -0 == +0
+                if ((v & 0x80000000u) || v > 0x7f800000u) ok = false;  // negative or NaN
+            }
+            const uint32_t prev = __shfl_up_sync(FULL, v, 1);
+            if (klane && lane > 0 && prev > v) ok = false;              // not ascending
+            bad = !__all_sync(FULL, ok);
+            epsb[lane] = v;
+            if (bad && lane == 0) set_status(a.status, 8 /*UNSORTED*/);
+            // rank table: the widest buckets that still separate every pair
+            // of distinct thresholds
+            tshift = 22;
+            for (; tshift > 0; --tshift) {
+                const bool clash = klane && lane > 0 && prev != v && (prev >> tshift) == (v >> tshift);
+                if (!__any_sync(FULL, clash)) break;
+            }
+            const uint32_t vmin = __shfl_sync(FULL, v, 0), vmax = __shfl_sync(FULL, v, K - 1);
+            const int tbase = (int)(vmin >> tshift);
+            tbm1 = tbase - 1;
+            tnb = (int)(vmax >> tshift) - tbase + 1;
+            tmul = tshift > 0 ? 1u << (32 - tshift) : 0u;
+            use_tab = !bad && tshift > 0 && tnb + 2 <= TMAX;
+            __syncwarp();
+            if (use_tab) {
+                // entry: rank of a key up to the bucket's threshold (bits 0-4),
+                // rank of a key above it (bits 5-9), the threshold's offset
+                // inside the bucket in the top tshift bits
+                for (int q = lane; q < tnb + 2; q += 32) {
+                    uint32_t e;
+                    if (q == 0) {
+                        e = 0u;                    // below every threshold's bucket
+                    } else if (q == tnb + 1) {
+                        e = (uint32_t)K | ((uint32_t)K << 5);  // above: all K thresholds are smaller
+                    } else {
+                        uint32_t rlo = 0, cnt = 0, off = 0;
+                        for (int k = 0; k < K; ++k) {
+                            const uint32_t ek = epsb[k];
+                            const int eb = (int)(ek >> tshift) - tbase;
+                            if (eb < q - 1) ++rlo;
+                            else if (eb == q - 1) { ++cnt; off = ek * tmul; }
+                        }
+                        e = rlo | ((rlo + cnt) << 5) | off;
+                    }
+                    tab[q] = e;
+                }
+            }
+            __syncwarp();
+        }
+        if (bad) continue;
+
+        const float *ys = a.y + sd.off;
+        // the full histogram row of threshold k (lane-independent base)
+        const int64_t hrow = sd.ne - 1 + (VERT && lb.loi ? 1 : 0);
+        uint64_t *const hbase =
+            lb.hist ? lb.hist + lb.hist_off[s] + (int64_t)lb.k0 * hrow : nullptr;
+        uint64_t *const gshort = lb.hshort + ((int64_t)s * lb.kstride + lb.k0) * LSH;
+
+        // lane k: a line of threshold k longer than WSH (rare): its length
+        // into the series' short histogram or the caller's full one
+        auto emit_rare = [&](uint32_t len) {
+            lmx = max(lmx, len);
+            lmass += len;
+            if (len <= (uint32_t)LSH)
+                atomicAdd(reinterpret_cast<unsigned long long *>(gshort + (int64_t)lane * LSH + (len - 1)),
+                          1ull);
+            else if (hbase)
+                atomicAdd(reinterpret_cast<unsigned long long *>(hbase + (int64_t)lane * hrow + (len - 1)),
+                          1ull);
+        };
+
+        // Lines of length >= 4.  Lane j's mask has bit k when slot [k][j]
+        // holds the word of threshold k of diagonal j; a bit transpose hands
+        // lane k the diagonals of its threshold, so every lane adds to its own
+        // histogram column.  In a slot, a line ends at row t - 1 for each bit t
+        // of the end mask; its first row follows the nearest non-recurrent row
+        // above, or it continues the run open above the word (bit 0: a line
+        // ending at the previous word's last row).
+        //
+        // The loop is warp-uniform (its condition is a vote) and takes at most
+        // one line per lane per turn with predicated steps and a predicated
+        // shared reduction, so no lane's data steers the warp's control flow;
+        // only a line longer than WSH branches.
+        auto long_lines = [&](uint32_t mask) {
+            if (!__any_sync(FULL, mask != 0u)) return;
+            __syncwarp();  // every lane's slots written before other lanes read them
+            uint32_t diag = transpose32(mask, lane);  // lane k: diagonals j with lines
+            uint32_t x = 0, wq = 0, cq = 0;           // the slot being read
+            const uint32_t hcol = static_cast<uint32_t>(__cvta_generic_to_shared(hs));
+            while (__any_sync(FULL, (x | diag) != 0u)) {
+                if (x == 0u && diag != 0u) {  // the next diagonal's slot
+                    const int j = __ffs(diag) - 1;
+                    diag &= diag - 1u;
+                    const uint2 q = lqa[lane * LD + j];
+                    x = q.x;
+                    cq = q.y;
+                    const uint4 b4 = *reinterpret_cast<const uint4 *>(pl + j * 4);
+                    wq = rank_le_word_lane(b4.x, b4.y, b4.z, b4.w, pl4[j], kbm);
+                }
+                const bool has = x != 0u;
+                const int t = (__ffs(x) - 1) & 31;
+                const uint32_t zb = ~wq & ((1u << t) - 1u);
+                const uint32_t len = zb ? (uint32_t)(t - 32 + __clz(zb)) : (uint32_t)t + cq;
+                x &= x - 1u;
+                red_shared_addr_if(hcol + min(len, (uint32_t)WSH) * 128u, has && len <= (uint32_t)WSH);
+                if (has && len > (uint32_t)WSH) emit_rare(len);
+            }
+            __syncwarp();  // slots are rewritten by the next block
+        };
+
+        // the unit's bands; the rank method is fixed per unit (branch hoisted)
+        auto bands = [&](auto use_table) {
+            constexpr bool TABLE = decltype(use_table)::value;
+            auto rank_of = [&](uint32_t key) -> uint32_t {
+                if (TABLE) {
+                    const uint64_t pk = (uint64_t)key * tmul;
+                    // bucket - (tbase - 1) clamped to [0, tnb + 1]: max(min(a + b, c), 0)
+                    const int q = __viaddmin_s32_relu((int)(uint32_t)(pk >> 32), -tbm1, tnb + 1);
+                    const uint32_t e = tab[q];
+                    return ((uint32_t)pk > e) ? (e >> 5) : e;  // bits 0-4: the rank
+                }
+                uint32_t rk = 0;
+                rk += (epsb[rk + 15] < key) ? 16u : 0u;
+                rk += (epsb[rk + 7] < key) ? 8u : 0u;
+                rk += (epsb[rk + 3] < key) ? 4u : 0u;
+                rk += (epsb[rk + 1] < key) ? 2u : 0u;
+                rk += (epsb[rk] < key) ? 1u : 0u;
+                return rk;
+            };
+            for (int b = ub_lo; b < ub_hi; ++b) {
+                const int d_lo = 1 + b * LD;                 // diagonal pass: first diagonal
+                const int c_lo = b * LD;                     // vertical pass: first column
+                const int rows = VERT ? sd.ne : sd.ne - d_lo;  // rows of the band's longest line
+                uint32_t st[KT];
+#pragma unroll
+                for (int k = 0; k < KT; ++k) st[k] = 0;
+
+                // cell phase of the 32 rows i0..i0+31: bit planes of the ranks
+                // of every diagonal into pl / pl4.  INTERIOR: every cell of the
+                // block inside the triangle (no bounds checks).
+                auto cell_phase = [&](int i0, auto interior) {
+                    constexpr bool INTERIOR = decltype(interior)::value;
+                    const int i = i0 + lane;
+#pragma unroll 1
+                    for (int jc = 0; jc < LD; jc += JC) {
+                        BandTile<M, TAU, JC> tile;
+                        if (VERT) {
+                            if (INTERIOR) tile.load_vert_fast(ys, i, c_lo + jc, sd.tau);
+                            else tile.load_vert(ys, sd.n, sd.ne, i, c_lo + jc, sd.tau);
+                        } else {
+                            if (INTERIOR) tile.load_fast(ys, i, d_lo + jc, sd.tau);
+                            else tile.load(ys, sd.n, i, d_lo + jc, rows, sd.tau, sd.m);
+                        }
+                        uint32_t g4[4];  // plane 4 of four consecutive diagonals: one store
+#pragma unroll
+                        for (int j = 0; j < JC; ++j) {
+                            const int col = c_lo + jc + j;   // vertical pass: column
+                            // diagonal pass: cell (i, i + dl); vertical: (i, col)
+                            const int dl = VERT ? col - i : d_lo + jc + j;
+                            const bool valid =
+                                VERT ? (INTERIOR || (i < sd.ne && col < sd.ne)) && (lb.loi || dl != 0)
+                                     : INTERIOR || i < sd.ne - dl;
+                            uint32_t r = 31;  // outside the matrix: recurrent for no k
+                            // register windows read no memory per cell, so cells
+                            // outside the triangle are computed and discarded
+                            if (TAU > 0 || valid) {
+                                const uint32_t key =
+                                    __float_as_uint(tile.dist(ys, j, i, dl, sd.tau, sd.m));
+                                const uint32_t rk = rank_of(key);
+                                r = valid ? rk : 31u;
+                            }
+                            const uint32_t B0 = __ballot_sync(FULL, r & 1u);
+                            const uint32_t B1 = __ballot_sync(FULL, r & 2u);
+                            const uint32_t B2 = __ballot_sync(FULL, r & 4u);
+                            const uint32_t B3 = __ballot_sync(FULL, r & 8u);
+                            g4[j & 3] = __ballot_sync(FULL, r & 16u);
+                            if (lane == 0) {
+                                *reinterpret_cast<uint4 *>(pl + (jc + j) * 4) = make_uint4(B0, B1, B2, B3);
+                                if ((j & 3) == 3)
+                                    *reinterpret_cast<uint4 *>(pl4 + jc + j - 3) =
+                                        make_uint4(g4[0], g4[1], g4[2], g4[3]);
+                            }
+                        }
+                    }
+                };
+
+                // run phase of the same 32 rows: lane j takes diagonal j
+                auto run_phase = [&]() {
+                    __syncwarp();
+                    const uint4 q = *reinterpret_cast<const uint4 *>(pl + lane * 4);
+                    const uint32_t B[5] = {q.x, q.y, q.z, q.w, pl4[lane]};
+                    __syncwarp();  // the next block's stores wait for these loads
+                    uint32_t lmask = 0;  // thresholds whose word ends lines of length >= 4
+#pragma unroll
+                    for (int k = 0; k < KT; ++k) {
+                        if (k < K) {
+                            const uint32_t w = rank_le_word(B, k);
+                            const uint32_t s0 = st[k];
+                            // row t of p_n = row t - n (rows above the block: the
+                            // previous word's top four rows, kept in the state)
+                            const uint32_t p1 = __funnelshift_l(s0, w, 1);
+                            const uint32_t p2 = __funnelshift_l(s0, w, 2);
+                            const uint32_t p3 = __funnelshift_l(s0, w, 3);
+                            const uint32_t p4 = __funnelshift_l(s0, w, 4);
+                            // bit t: a line ends at row t - 1 (t = 0: the previous
+                            // block's last row) and is at least 1, 2, 3, 4 long
+                            const uint32_t e1 = p1 & ~w;
+                            const uint32_t e2 = e1 & p2;
+                            const uint32_t e3 = e2 & p3;
+                            const uint32_t e4 = e3 & p4;
+                            // lines of length >= 4 are counted by length below, not here
+                            tal[k] += __popc(e1) + (__popc(e2) << 10) + (__popc(e3) << 20) -
+                                      __popc(e4) * 0x100401u;
+                            if (e4) {  // measured after the loop (rare for noisy series)
+                                lq[k * LD] = make_uint2(e4, s0 & CMASK);
+                                lmask |= 1u << k;
+                            }
+                            // the new state: top rows of this word and the run open at its last row
+                            const uint32_t open = (w == FULL) ? (s0 & CMASK) + 32u : (uint32_t)__clz(~w);
+                            st[k] = (w & TOP4) | open;
+                        }
+                    }
+                    long_lines(lmask);
+                };
+
+                // the packed tallies take SETTLE row blocks before a field could overflow
+                int i0 = 0;
+                // interior row blocks: every cell of the block inside the matrix
+                const int i_end = VERT ? (c_lo + LD <= sd.ne ? rows - 31 : 0) : rows - (LD - 1) - 31;
+                for (; i0 < i_end; i0 += 32) {
+                    cell_phase(i0, std::true_type{});
+                    run_phase();
+                    if (++nrb == SETTLE) settle();
+                }
+                for (; i0 < rows; i0 += 32) {
+                    cell_phase(i0, std::false_type{});
+                    run_phase();
+                    if (++nrb == SETTLE) settle();
+                }
+                // lines that reach the end of a diagonal exactly at a block's last
+                // row: a line of length c ending just above a word (end bit 0)
+                uint32_t bmask = 0;
+#pragma unroll
+                for (int k = 0; k < KT; ++k) {
+                    if (k < K) {
+                        const uint32_t c = st[k] & CMASK;
+                        if (c >= 4) {
+                            lq[k * LD] = make_uint2(1u, c);
+                            bmask |= 1u << k;
+                        } else {
+                            tal[k] += c == 0 ? 0u : c == 1 ? 1u : c == 2 ? 0x401u : 0x100401u;
+                        }
+                    }
+                }
+                long_lines(bmask);
+            }
+        };
+        if (use_tab) bands(std::true_type{});
+        else bands(std::false_type{});
+        // flush after each unit: a warp's next unit is usually another series
+        flush();
+        cur = -1;
+    }
+    flush();
+}
+
+}  // namespace rqa
+
+namespace rqa {
+using LinesKernel = void (*)(CellArgs, LineBufs, int);
+// Instantiations, one group per translation unit (they compile in parallel).
+LinesKernel lines_kernel_m3t3(int tile, bool vert);
+LinesKernel lines_kernel_m3t1(int tile, bool vert);
+LinesKernel lines_kernel_m1t1(int tile, bool vert);
+LinesKernel lines_kernel_generic(int m, bool vert);
+}  // namespace rqa

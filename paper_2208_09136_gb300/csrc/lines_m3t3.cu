@@ -1,0 +1,18 @@
+// Instantiations of the line pass kernel (lines_kernel.cuh) for m = 3, tau = 3:
+// the diagonal pass with register windows of 8, 16 and 32 diagonals, and the
+// vertical pass.  One group per translation unit, so they compile in parallel.
+#include "lines_kernel.cuh"
+
+namespace rqa {
+
+LinesKernel lines_kernel_m3t3(int tile, bool vert)
+{
+    if (vert) return k_lines<3, 3, LINE_TILE_DEFAULT, true>;
+    switch (tile) {
+    case 8: return k_lines<3, 3, 8, false>;
+    case 32: return k_lines<3, 3, 32, false>;
+    default: return k_lines<3, 3, LINE_TILE_DEFAULT, false>;
+    }
+}
+
+}  // namespace rqa

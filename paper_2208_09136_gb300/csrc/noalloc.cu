@@ -9,6 +9,7 @@
 // histograms, tables, work items and counters in g_scratch below, which
 // exists from the moment the library is loaded on a device until the process
 // exits.  Inputs and outputs are the caller's.
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -21,6 +22,10 @@ namespace {
 
 constexpr int NA_MAX_S = RQA_NOALLOC_MAX_SERIES;
 constexpr int NA_MAX_ITEMS_PER_SERIES = 1024;
+// Cells of one work item at most: the counting kernels histogram an item in
+// 32-bit shared bins, so an item of more cells could wrap a bin that holds
+// most of its keys (a constant or heavily quantised series).
+constexpr uint64_t NA_ITEM_CELLS_MAX = (uint64_t)1 << 30;
 constexpr int NA_KMAX = RQA_NOALLOC_K_MAX;  // targets per call here (one middle-round launch)
 static_assert(NA_KMAX < MID_GROUPS && NA_KMAX >= NSUB_MAX, "fixed-scratch layout assumptions");
 
@@ -68,6 +73,19 @@ struct NaDevice {
 constexpr int NA_MAX_DEVICES = 64;
 NaDevice g_dev[NA_MAX_DEVICES];
 std::mutex g_dev_mu;
+
+// A pointer the kernels dereference must be memory the current device can
+// address: its own device memory, or managed memory.
+bool na_device_ptr(const void *p, int device)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == device;
+}
 
 int na_setup(int device, NaDevice &out)
 {
@@ -154,6 +172,7 @@ extern "C" int rqa_eps_for_rr_noalloc(const rqa_batch *b, const int32_t *rr_num,
         if (n > (int64_t)0x7fffffff - 64) return RQA_ERR_CAPACITY;
         const int64_t ne = n - (int64_t)(b->m[s] - 1) * b->tau[s];
         if (ne < 2) return RQA_ERR_TOO_SHORT;
+        if (ne > RQA_NOALLOC_NE_MAX) return RQA_ERR_CAPACITY;
         SeriesDev &d = pl.sd[s];
         d.off = b->offsets[s];
         d.n = (int32_t)n;
@@ -166,6 +185,10 @@ extern "C" int rqa_eps_for_rr_noalloc(const rqa_batch *b, const int32_t *rr_num,
         // at least four bands per warp, at most NA_MAX_ITEMS_PER_SERIES items
         int chunk = 4 * WARPS;
         while ((d.nbands + chunk - 1) / chunk > NA_MAX_ITEMS_PER_SERIES) chunk *= 2;
+        // the largest item is the first (the longest diagonals 1..chunk*BAND);
+        // every Ne up to RQA_NOALLOC_NE_MAX passes, this guards the invariant
+        const int64_t dl = std::min<int64_t>((int64_t)chunk * BAND, ne - 1);
+        if ((uint64_t)(dl * ne - dl * (dl + 1) / 2) > NA_ITEM_CELLS_MAX) return RQA_ERR_CAPACITY;
         pl.chunk[s] = chunk;
         pl.item_begin[s] = n_items;
         n_items += (d.nbands + chunk - 1) / chunk;
@@ -177,6 +200,10 @@ extern "C" int rqa_eps_for_rr_noalloc(const rqa_batch *b, const int32_t *rr_num,
         cudaGetLastError();
         return RQA_ERR_CUDA;
     }
+    if (!na_device_ptr(b->y, device) || !na_device_ptr(eps_out, device) ||
+        (count_le && !na_device_ptr(count_le, device)) || (count_lt && !na_device_ptr(count_lt, device)) ||
+        (status_out && !na_device_ptr(status_out, device)))
+        return RQA_ERR_INVALID_ARG;
     NaDevice dv;
     if (int rc = na_setup(device, dv)) return rc;
     unsigned char *scr = dv.scratch;

@@ -14,6 +14,38 @@ __device__ __forceinline__ void set_status(int *status, int code)
     atomicCAS(status, 0, code);
 }
 
+// Add 1 to the shared word at shared-space address a when pred holds, as
+// one predicated reduction (no branch, so a warp whose lanes disagree does
+// not split; a is not touched when pred is false).
+__device__ __forceinline__ void red_shared_addr_if(uint32_t a, bool pred)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\t@q red.shared.add.u32 [%0], 1;\n\t}"
+                 :: "r"(a), "r"((uint32_t)pred) : "memory");
+}
+
+// max(a, b, c) in one instruction (three-input FP32 max of sm_100 and later);
+// exact, like two two-input maxima.
+__device__ __forceinline__ float fmax3(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// Maximum norm of the M per-coordinate differences a[q] - b[q] (Sect. 2):
+// absolute values folded into the maxima, three at a time.
+template <int M>
+__device__ __forceinline__ float maxnorm(const float (&diff)[M])
+{
+    float d = fabsf(diff[0]);
+    int q = 1;
+#pragma unroll
+    for (; q + 1 < M; q += 2) d = fmax3(d, fabsf(diff[q]), fabsf(diff[q + 1]));
+#pragma unroll
+    for (; q < M; ++q) d = fmaxf(d, fabsf(diff[q]));
+    return d;
+}
+
 // Distances of one lane's cells in a band: row i (lane), diagonals
 // d_lo .. d_lo+D-1.  Maximum-norm distance (Sect. 2) with FP32 subtract, abs
 // and max only, so every value is exact and equal to a CPU evaluation.
@@ -70,10 +102,10 @@ struct BandTile {
     __device__ __forceinline__ float dist(const float *__restrict__, int j, int, int, int,
                                           int) const
     {
-        float d = fabsf(a[0] - w[j]);
+        float diff[M];
 #pragma unroll
-        for (int q = 1; q < M; ++q) d = fmaxf(d, fabsf(a[q] - w[j + q * TAU]));
-        return d;
+        for (int q = 0; q < M; ++q) diff[q] = a[q] - w[j + q * TAU];
+        return maxnorm<M>(diff);
     }
 };
 
@@ -110,10 +142,10 @@ struct BandTile<M, 0, D> {
                                           int tau, int) const
     {
         const int j = i + dl;
-        float d = fabsf(a[0] - __ldg(ys + j));
+        float diff[M];
 #pragma unroll
-        for (int q = 1; q < M; ++q) d = fmaxf(d, fabsf(a[q] - __ldg(ys + j + q * tau)));
-        return d;
+        for (int q = 0; q < M; ++q) diff[q] = a[q] - __ldg(ys + j + q * tau);
+        return maxnorm<M>(diff);
     }
 };
 

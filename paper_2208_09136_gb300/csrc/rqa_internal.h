@@ -10,7 +10,8 @@ namespace rqa {
 // 11-bit coarse digit (bits 30..20), a 10-bit middle digit (19..10) and a
 // 10-bit low digit (9..0).
 constexpr int KMAX = 127;        // targets per series and call
-constexpr int LINE_KMAX = 31;    // targets per line-pass launch (lanes of a warp, 5-bit ranks)
+constexpr int LINE_KMAX = 20;    // targets per line-pass sweep (per-lane run state in registers)
+constexpr int LINE_BAND = 32;    // diagonals (columns) per warp band of the line pass: one per lane
 constexpr int MID_GROUPS = 48;   // middle-round groups per launch (4 KB of shared bins each)
 constexpr int COARSE_SHIFT = 20;
 constexpr int NCOARSE = 1 << 11;   // 2048 coarse buckets
@@ -22,7 +23,8 @@ constexpr int LSH = 64;            // line lengths 1..LSH counted in shared memo
 constexpr int LMIN_MAX = 8;        // entries of an lmin list
 constexpr int THREADS = 256;       // threads per CTA of the cell kernels
 constexpr int BAND = 16;           // diagonals per warp band of the counting rounds
-constexpr int DL_DEFAULT = 4;      // diagonals per warp band of the line pass
+constexpr int LINE_TILE_DEFAULT = 16;  // diagonals per register window of the line pass's cell phase
+constexpr int LINE_NE_MAX = (1 << 26) - 1;  // vectors per series the line pass counts exactly
 constexpr int WARPS = THREADS / 32;
 
 // Counting rounds of the selection.
@@ -83,7 +85,7 @@ struct CellArgs {
     const int64_t *uprefix;  // n_pos + 1 prefix of unit counts along order
     int32_t n_pos;
     int32_t chunk;           // bands per unit
-    int32_t band_lines;      // diagonals per band of the line pass (4, 8 or 16)
+    int32_t line_tile;       // diagonals per register window of the line pass (8, 16 or 32)
     int64_t n_units;
     unsigned int *queue;   // ticket counter (64-bit aligned), zeroed before launch
     int *status;
@@ -111,11 +113,11 @@ struct LineBufs {
 };
 cudaError_t launch_lines(const CellArgs &a, const LineBufs &lb, int K, int grid, int embed,
                          cudaStream_t st);
-// Vertical lines of the whole matrix: the same warp pass over bands of D = 4
-// columns (every row of each), reusing the diagonal pass's work plan.
+// Vertical lines of the whole matrix: the same warp pass over bands of
+// LINE_BAND columns (every row of each), reusing the diagonal pass's work plan.
 cudaError_t launch_vlines(const CellArgs &a, const LineBufs &lb, int K, int grid, int embed,
                           cudaStream_t st);
-bool lines_band_ok(int embed, int band);
+bool lines_tile_ok(int embed, int tile);
 cudaError_t launch_finalize_det(const LineBufs &lb, const SeriesDev *series, int S, int K,
                                 const int32_t *lmin_dev, int n_lmin, double *det,
                                 double *det_avg, bool loi, cudaStream_t st);

@@ -27,10 +27,13 @@ cudaError_t mlp_backward(const float *params, const float *X, const float *acts,
                          float *loss, float *scratch, cudaStream_t st);
 cudaError_t adam_step(float *p, const float *g, float *m, float *v, int64_t n, int t, float lr,
                       float b1, float b2, float eps, cudaStream_t st);
-// also writes range[2s], range[2s+1]: the keys of the split buckets' span
+// also writes range[2s], range[2s+1]: the keys of the split buckets' span.
+// dom[s] == 0: series s is not bracketed (no split bucket, empty range).
 cudaError_t launch_bracket(const float *Y, const float *centre, float margin, int S, int K,
-                           int8_t *tab_sub, int32_t *n_sub, uint32_t *range, cudaStream_t st);
-cudaError_t launch_bracket_stats(const uint8_t *level, int64_t n, unsigned long long *hm,
-                                 cudaStream_t st);
+                           const uint8_t *dom, int8_t *tab_sub, int32_t *n_sub, uint32_t *range,
+                           cudaStream_t st);
+// hits / misses over the S x K levels of the series with dom[s] != 0
+cudaError_t launch_bracket_stats(const uint8_t *level, const uint8_t *dom, int S, int K,
+                                 unsigned long long *hm, cudaStream_t st);
 
 }  // namespace rqa

@@ -52,14 +52,6 @@ int count_smem_bytes(int round, int K)
     }
 }
 
-// Add 1 to the shared word at shared-space address a when pred holds, as
-// one predicated reduction (no branch, so a warp whose lanes disagree does
-// not split; a is not touched when pred is false).
-__device__ __forceinline__ void red_shared_addr_if(uint32_t a, bool pred)
-{
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\t@q red.shared.add.u32 [%0], 1;\n\t}"
-                 :: "r"(a), "r"((uint32_t)pred) : "memory");
-}
 __device__ __forceinline__ void red_shared_if(uint32_t *p, bool pred)
 {
     red_shared_addr_if(static_cast<uint32_t>(__cvta_generic_to_shared(p)), pred);

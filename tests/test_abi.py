@@ -93,7 +93,8 @@ def test_binding_constants_match_header():
     text = open(os.path.join(ROOT, "include", "rqa.h")).read()
     defines = {k: int(v) for k, v in re.findall(r"#define\s+(RQA_[A-Z0-9_]+)\s+(\d+)", text)}
     mirrored = [k for k in defines if hasattr(abi, k)]
-    assert {"RQA_K_MAX", "RQA_FLAG_NO_GRAPHS", "RQA_FLAG_LOI", "RQA_NOALLOC_K_MAX"} <= set(mirrored)
+    assert {"RQA_K_MAX", "RQA_FLAG_NO_GRAPHS", "RQA_FLAG_LOI", "RQA_NOALLOC_K_MAX",
+            "RQA_NOALLOC_NE_MAX"} <= set(mirrored)
     for k in mirrored:
         assert getattr(abi, k) == defines[k], k
 
@@ -114,3 +115,34 @@ def test_target_counts_loi_match_oracle(built, ne):
         assert np.array_equal(rqa.rqa_target_counts_loi(ne, rr, den), want)
     with pytest.raises(rqa.RqaError):
         rqa.rqa_target_counts_loi((1 << 32) + 1, [50], 100)
+
+
+def test_noalloc_rejects_series_beyond_its_item_limit(built):
+    """The fixed-scratch entry point checks every size on the host before it
+    touches the device: a series with Ne > RQA_NOALLOC_NE_MAX (its work items
+    would pass 2^30 cells, beyond what 32-bit shared counts hold exactly) is
+    RQA_ERR_CAPACITY, and so is one series too many; an ordinary size gets past
+    those checks (to the CUDA calls, which fail here without a GPU)."""
+    import ctypes
+    import torch
+    from paper_2208_09136_gb300 import abi
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the device path would run")
+    L = abi.lib()
+    rr = np.arange(1, 21, dtype=np.int32)
+    dummy = np.zeros(4, dtype=np.float32)  # never dereferenced: the checks fail first
+
+    def call(lengths, m=1, tau=1):
+        offs = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+        ms = np.full(len(lengths), m, dtype=np.int32)
+        taus = np.full(len(lengths), tau, dtype=np.int32)
+        b = abi._Batch(dummy.ctypes.data, offs.ctypes.data, ms.ctypes.data, taus.ctypes.data,
+                       len(lengths))
+        return L.rqa_eps_for_rr_noalloc(ctypes.byref(b), rr.ctypes.data, 100, 20,
+                                        ctypes.c_void_p(dummy.ctypes.data), None, None, None, None)
+
+    ne_max = abi.RQA_NOALLOC_NE_MAX
+    assert call([ne_max + 1]) == 7                 # RQA_ERR_CAPACITY
+    assert call([100, ne_max + 3], m=3, tau=1) == 7  # Ne = ne_max + 1 in the second series
+    assert call([100] * (abi.RQA_NOALLOC_MAX_SERIES + 1)) == 7
+    assert call([ne_max]) == 4                     # accepted sizes reach the device: RQA_ERR_CUDA

@@ -1,4 +1,4 @@
-"""CUDA-graph replay of rqa_det_avg and the line-pass band autotuner.
+"""CUDA-graph replay of rqa_det_avg and the line-pass autotuner.
 
 A call with the same arguments as the previous one on a caller-owned stream
 replays the recorded launch sequence; every decision of the sequence is taken
@@ -156,20 +156,20 @@ def test_changed_arguments_record_again(rqa_lib):
     ctx.close()
 
 
-def test_autotune_picks_a_supported_band_and_stays_exact(rqa_lib):
+def test_autotune_picks_a_supported_tile_and_stays_exact(rqa_lib):
     import torch
     rqa = rqa_lib
     stream = torch.cuda.Stream()
     ys = _series(13, [6000, 800, 4000])
     ctx = rqa.Context(stream=stream, select=rqa.RQA_SELECT_RADIX)
     run = _Run(rqa, ctx, ys, 3, 3, stream)
-    band = rqa.rqa_autotune(ctx, run.batch, RR20, 100)
-    assert band in (4, 8, 16)
-    assert rqa.rqa_device_info(ctx)["band"] == band
+    tile = rqa.rqa_autotune(ctx, run.batch, RR20, 100)
+    assert tile in (8, 16, 32)
+    assert rqa.rqa_device_info(ctx)["tile"] == tile
     res = run.call()
     _against_oracle(res, ys, 3, 3)
-    # a context created with an explicit band keeps it
-    ctx2 = rqa.Context(stream=stream, select=rqa.RQA_SELECT_RADIX, band=8)
+    # a context created with an explicit tile keeps it
+    ctx2 = rqa.Context(stream=stream, select=rqa.RQA_SELECT_RADIX, tile=8)
     assert rqa.rqa_autotune(ctx2, run.batch, RR20, 100) == 8
     ctx.close()
     ctx2.close()

@@ -141,6 +141,34 @@ def test_schedules_agree_bitwise(rqa_lib):
         assert np.array_equal(a["hist"][s], b["hist"][s])
 
 
+def test_det_nan_without_recurrences(rqa_lib):
+    """Caller thresholds below every distance leave C_k = 0: DET_k is then 0/0,
+    NaN on both sides, and so is the average over the targets; the other
+    targets and series stay finite and bit-exact."""
+    import torch
+    import paper_2208_09136_gb300 as rqa
+    from oracle import rqa_oracle as O
+    rng = np.random.default_rng(21)
+    ys = [np.cumsum(rng.uniform(1.0, 2.0, 300)).astype(np.float32),  # every |step| >= 1
+          rng.standard_normal(500).astype(np.float32)]
+    eps_np = np.array([[0.5, 3.0], [0.05, 0.2]], dtype=np.float32)
+    ctx = rqa.Context(device=0)
+    batch = rqa.Batch.from_numpy(ys, 1, 1)
+    eps = torch.from_numpy(eps_np).cuda()
+    out = rqa.det_avg(ctx, batch, None, 0, lmin=(2, 3), eps=eps, K=2, lines=True)
+    assert rqa.rqa_status(ctx) == 0
+    det = out["det"].cpu().numpy()
+    avg = out["det_avg"].cpu().numpy()
+    for s, y in enumerate(ys):
+        lines = O.line_hist(y, 1, 1, eps_np[s])
+        ref = O.det_from_hist(lines["hist"], lines["count"], (2, 3))
+        assert np.array_equal(det[s], ref, equal_nan=True), (s, det[s], ref)
+        assert np.array_equal(avg[s], O.det_avg(ref), equal_nan=True)
+        assert np.array_equal(out["count"].cpu().numpy()[s], lines["count"])
+    assert np.isnan(det[0, 0]).all() and np.isfinite(det[0, 1]).all()
+    ctx.close()
+
+
 def test_device_errors_reported(rqa_lib):
     import torch
     import paper_2208_09136_gb300 as rqa
@@ -172,8 +200,8 @@ def test_device_errors_reported(rqa_lib):
 @pytest.mark.parametrize("schedule", SCHEDS)
 def test_rr_up_to_99(rqa_lib, schedule):
     """RR = 1..99 % (Sect. 2 averages up to RR* = 99): 99 targets per call,
-    middle round in windows of 48 groups and the line pass in four sweeps of
-    at most 31 targets; bit-exact against the oracle."""
+    middle round in windows of 48 groups and the line pass in five sweeps of
+    at most 20 targets; bit-exact against the oracle."""
     rng = np.random.default_rng(99)
     ys = [rng.standard_normal(300).astype(np.float32),
           (np.sin(2 * np.pi * np.arange(1500) / 20.3) + 0.3 * rng.standard_normal(1500)).astype(np.float32),
@@ -185,10 +213,11 @@ def test_rr_up_to_99(rqa_lib, schedule):
         assert_series_equal(g, s, ref, "RR 1..99")
 
 
-@pytest.mark.parametrize("K", [31, 32, 62, 63, 127])
+@pytest.mark.parametrize("K", [20, 21, 31, 32, 40, 41, 62, 63, 127])
 def test_target_count_group_boundaries(rqa_lib, K):
-    """K around the 31-target line-pass groups and the 48-group middle-round
-    windows, up to K = RQA_K_MAX = 127 (rr_den = 128)."""
+    """K around the 20-target line-pass sweeps, the 31-target fixed-scratch
+    limit and the 48-group middle-round windows, up to K = RQA_K_MAX = 127
+    (rr_den = 128)."""
     rng = np.random.default_rng(K)
     ys = [rng.standard_normal(400).astype(np.float32), rng.standard_normal(77).astype(np.float32)]
     rr = list(range(1, K + 1))
