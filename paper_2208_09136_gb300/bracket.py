@@ -7,10 +7,12 @@ the library's own kernels only: exact thresholds from ``rqa_eps_for_rr``
 ``rqa_mlp_forward`` / ``rqa_mlp_backward`` / ``rqa_adam_step`` fit it with
 the pinball loss at quantiles tau_lo / tau_hi.  PyTorch only allocates.
 
-Model file: 8-byte magic ``RQAMLP01``, uint32 parameter count, float32
-margin, float32 tau_lo, float32 tau_hi, the float32 parameters, uint32
-CRC-32 of the parameter bytes.  ``python -m paper_2208_09136_gb300.bracket
-train --out FILE`` trains one.
+Model file: 8-byte magic ``RQAMLP02``, uint32 parameter count, float32
+margin, float32 tau_lo, float32 tau_hi, uint32 number of training
+embeddings n, n pairs of int32 (m, tau), the float32 parameters, uint32
+CRC-32 of the embedding and parameter bytes.  (``RQAMLP01`` files, without
+the embeddings, load with an unrestricted domain.)  ``python -m
+paper_2208_09136_gb300.bracket train --out FILE`` trains one.
 """
 from __future__ import annotations
 
@@ -28,7 +30,8 @@ import numpy as np
 
 from . import abi
 
-MAGIC = b"RQAMLP01"
+MAGIC = b"RQAMLP02"
+MAGIC_V1 = b"RQAMLP01"
 MODEL_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "models")
 MODEL_PATH = os.path.join(MODEL_DIR, "bracket_mlp.bin")
 RR = list(range(1, 21))
@@ -36,39 +39,53 @@ LAYERS = [(131, 256), (256, 256), (256, 40)]
 TINY = 2.0 ** -126
 
 
-def save_model(path: str, params: np.ndarray, margin: float, tau_lo: float, tau_hi: float):
+def save_model(path: str, params: np.ndarray, margin: float, tau_lo: float, tau_hi: float,
+               domain=((3, 3),)):
+    """domain: the (m, tau) embeddings of the training series."""
     params = np.ascontiguousarray(params, dtype=np.float32)
     assert params.size == abi.RQA_MLP_PARAMS
     os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
-    body = params.tobytes()
+    dom = np.ascontiguousarray(list(domain), dtype=np.int32).reshape(-1, 2)
+    body = dom.tobytes() + params.tobytes()
     with open(path, "wb") as f:
         f.write(MAGIC)
         f.write(struct.pack("<Ifff", params.size, margin, tau_lo, tau_hi))
+        f.write(struct.pack("<I", dom.shape[0]))
         f.write(body)
         f.write(struct.pack("<I", zlib.crc32(body) & 0xFFFFFFFF))
 
 
 def load_model(path: str = MODEL_PATH) -> Dict[str, object]:
     raw = open(path, "rb").read()
-    if raw[:8] != MAGIC:
+    if raw[:8] not in (MAGIC, MAGIC_V1):
         raise ValueError(f"{path}: not a bracket model")
     n, margin, tau_lo, tau_hi = struct.unpack("<Ifff", raw[8:24])
-    if n != abi.RQA_MLP_PARAMS or len(raw) != 24 + 4 * n + 4:
+    pos, domain = 24, []
+    if raw[:8] == MAGIC:
+        (nd,) = struct.unpack("<I", raw[24:28])
+        pos = 28
+        dom = np.frombuffer(raw[pos:pos + 8 * nd], dtype=np.int32).reshape(-1, 2)
+        domain = [(int(a), int(b)) for a, b in dom]
+        pos += 8 * nd
+    if n != abi.RQA_MLP_PARAMS or len(raw) != pos + 4 * n + 4:
         raise ValueError(f"{path}: wrong size")
-    body = raw[24:24 + 4 * n]
-    (crc,) = struct.unpack("<I", raw[24 + 4 * n:])
+    body = raw[24 if raw[:8] == MAGIC_V1 else 28:pos + 4 * n]
+    (crc,) = struct.unpack("<I", raw[pos + 4 * n:])
     if zlib.crc32(body) & 0xFFFFFFFF != crc:
         raise ValueError(f"{path}: checksum mismatch")
-    return {"params": np.frombuffer(body, dtype=np.float32).copy(), "margin": margin,
-            "tau_lo": tau_lo, "tau_hi": tau_hi}
+    return {"params": np.frombuffer(raw[pos:pos + 4 * n], dtype=np.float32).copy(),
+            "margin": margin, "tau_lo": tau_lo, "tau_hi": tau_hi, "domain": domain}
 
 
 def install(ctx: abi.Context, path: str = MODEL_PATH, margin: Optional[float] = None):
-    """Load a model file and install it in a context; returns the model dict."""
+    """Load a model file and install it in a context, with its training
+    domain (RQA_SELECT_AUTO brackets only series with those embeddings);
+    returns the model dict."""
     import torch
     m = load_model(path)
     t = torch.from_numpy(m["params"]).to(f"cuda:{ctx.device}")
     abi.rqa_set_bracket_model(ctx, t, m["margin"] if margin is None else margin)
+    abi.rqa_set_bracket_domain(ctx, m["domain"])
     torch.cuda.synchronize(ctx.device)
     return m
 
@@ -162,7 +179,7 @@ def train(workload: str = "train-20000", epochs: int = 60, batch_size: int = 256
             log(f"epoch {ep:3d} val loss {vl['loss']:.5f} cover {vl['cover']:.4f} "
                 f"width {vl['width']:.4f} ({time.time() - t0:.1f} s)")
     out = {"params": params.cpu().numpy(), "tau_lo": tau_lo, "tau_hi": tau_hi, "val": hist[-1],
-           "seconds": time.time() - t0}
+           "seconds": time.time() - t0, "domain": sorted({(sp.m, sp.tau) for sp in specs})}
     ctx.close()
     return out
 
@@ -194,7 +211,7 @@ def main(argv=None):
     a = ap.parse_args(argv)
     if a.cmd == "train":
         res = train(a.workload, epochs=a.epochs, device=a.device)
-        save_model(a.out, res["params"], a.margin, res["tau_lo"], res["tau_hi"])
+        save_model(a.out, res["params"], a.margin, res["tau_lo"], res["tau_hi"], res["domain"])
         print(json.dumps({"saved": a.out, "val": res["val"], "seconds": res["seconds"],
                           "margin": a.margin}))
     return 0

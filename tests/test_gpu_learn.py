@@ -150,7 +150,11 @@ def test_bracket_rejects_other_targets(rqa_lib):
 def test_trained_model_hits_and_stays_exact(rqa_lib):
     """The trained network on held-out long Lorenz series (N = 10^5,
     m = tau = 3, SNR -10/0/10 dB): thresholds equal the radix selection bit
-    for bit, and most intervals hold (each miss costs one extra pass)."""
+    for bit and are proven exact by the oracle's counting certificate
+    #{d < eps_k} < T_k <= #{d <= eps_k} (one streaming pass over the 5*10^9
+    cells of each series, no sort), and most intervals hold (each miss costs
+    the full selection for its series)."""
+    from oracle import c_oracle as CO
     from paper_2208_09136_gb300 import bracket
     if not os.path.exists(bracket.MODEL_PATH):
         pytest.skip("no trained model file")
@@ -164,3 +168,92 @@ def test_trained_model_hits_and_stays_exact(rqa_lib):
         assert np.array_equal(got[key], base[key]), key
     assert hits + misses == 60
     assert hits >= 54, (hits, misses)
+    for s, y in enumerate(ys):
+        ne = len(y) - 6
+        P = ne * (ne - 1) // 2
+        T = np.array([-((-r * P) // 100) for r in RR20], dtype=np.int64)
+        le, lt = CO.count(y, 3, 3, got["eps"][s])
+        assert np.all(lt.astype(np.int64) < T) and np.all(T <= le.astype(np.int64)), s
+        assert np.array_equal(le, got["count_le"][s]) and np.array_equal(lt, got["count_lt"][s]), s
+
+
+def _timed_det_avg(rqa, ys, m, tau, learned, reps=2):
+    """Phase times (ms) of rqa_det_avg in the batched schedule, the fastest of
+    reps calls, and the call's outputs."""
+    import torch
+    from paper_2208_09136_gb300 import bracket
+    stream = torch.cuda.Stream()
+    ctx = rqa.Context(stream=stream, select=rqa.RQA_SELECT_AUTO if learned else rqa.RQA_SELECT_RADIX)
+    if learned:
+        bracket.install(ctx)
+    rqa.rqa_set_timing(ctx, True)
+    with torch.cuda.stream(stream):
+        batch = rqa.Batch.from_numpy(ys, m, tau)
+    best = None
+    for _ in range(reps + 1):
+        with torch.cuda.stream(stream):
+            out = rqa.det_avg(ctx, batch, RR20, 100, lmin=(2, 3, 5))
+        stream.synchronize()
+        ph = rqa.rqa_phase_times(ctx)
+        best = ph if best is None else np.minimum(best, ph)
+    assert rqa.rqa_status(ctx) == 0
+    stats = rqa.rqa_bracket_stats(ctx) if learned else None
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    ctx.close()
+    return best, res, stats
+
+
+def test_trained_model_gain_on_long_series(rqa_lib):
+    """What the trained network buys on the held-out long series: with its
+    intervals the selection skips the middle counting pass (its phase does no
+    work) and takes less time in all than the radix selection of the same
+    batched schedule, with identical outputs."""
+    from paper_2208_09136_gb300 import bracket
+    if not os.path.exists(bracket.MODEL_PATH):
+        pytest.skip("no trained model file")
+    from synth import workload
+    ys = workload("lorenz-n1e5-eval").series()
+    rad, r_out, _ = _timed_det_avg(rqa_lib, ys, 3, 3, False)
+    lrn, l_out, (hits, misses) = _timed_det_avg(rqa_lib, ys, 3, 3, True)
+    for key in ("eps", "det", "det_avg"):
+        assert np.array_equal(l_out[key], r_out[key]), key
+    assert hits == 60 and misses == 0, (hits, misses)
+    # phases: [1] coarse or bracket round + select, [2] middle round, [3] final round
+    assert lrn[2] < 0.05 * rad[2], (lrn, rad)
+    assert lrn[1] + lrn[2] + lrn[3] < rad[1] + rad[2] + rad[3], (lrn, rad)
+
+
+def test_auto_selection_keeps_to_the_training_domain(rqa_lib):
+    """RQA_SELECT_AUTO brackets only series whose embedding the network was
+    trained on (m = tau = 3 here): a batch of other embeddings runs the plain
+    selection (no bracketed target counted), a mixed batch brackets exactly
+    its m = tau = 3 series; results equal the radix selection bit for bit."""
+    import torch
+    rqa = rqa_lib
+    from paper_2208_09136_gb300 import bracket
+    if not os.path.exists(bracket.MODEL_PATH):
+        pytest.skip("no trained model file")
+    assert bracket.load_model()["domain"] == [(3, 3)]
+    ys = _series(41, [400, 2500, 1200, 800])
+    for m, tau, n_in in (([1, 1, 1, 1], [1, 1, 1, 1], 0), ([3, 3, 3, 3], [1, 1, 1, 1], 0),
+                         ([3, 3, 3, 1], [3, 1, 3, 1], 2)):
+        ctx = rqa.Context(select=rqa.RQA_SELECT_AUTO)
+        bracket.install(ctx)
+        batch = rqa.Batch.from_numpy(ys, m, tau)
+        got = rqa.eps_for_rr(ctx, batch, RR20, 100)
+        hits, misses = rqa.rqa_bracket_stats(ctx)
+        assert rqa.rqa_status(ctx) == 0
+        assert hits + misses == 20 * n_in, (m, tau, hits, misses)
+        ref_ctx = rqa.Context(select=rqa.RQA_SELECT_RADIX)
+        ref = rqa.eps_for_rr(ref_ctx, batch, RR20, 100)
+        for key in ("eps", "count_le", "count_lt"):
+            assert np.array_equal(got[key].cpu().numpy(), ref[key].cpu().numpy()), (key, m, tau)
+        ctx.close()
+        ref_ctx.close()
+    # the domain can be lifted: every series is bracketed again
+    ctx = rqa.Context(select=rqa.RQA_SELECT_AUTO)
+    bracket.install(ctx)
+    rqa.rqa_set_bracket_domain(ctx, [])
+    rqa.eps_for_rr(ctx, rqa.Batch.from_numpy(ys, 1, 1), RR20, 100)
+    assert sum(rqa.rqa_bracket_stats(ctx)) == 80
+    ctx.close()
