@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--workload", default="full-296")
     ap.add_argument("--form", default="auto", choices=["auto", "batched", "plain"])
     ap.add_argument("--no-plain", action="store_true", help="skip the per-series comparison")
+    ap.add_argument("--no-radix", action="store_true",
+                    help="skip the batched radix-selection comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-cells", type=float, default=1.2e8,
@@ -307,7 +309,8 @@ def main():
             dist.barrier()
 
     ctx = make_ctx(sched, have_model)
-    tuned_tile = rqa.rqa_autotune(ctx, batch, RR, 100)  # keeps --tile when one was given
+    from paper_2208_09136_gb300 import tuning
+    tuned = tuning.tuned(ctx, batch, RR, 100)  # cached or timed now; keeps --tile when one was given
     rqa.rqa_set_timing(ctx, True)
     for _ in range(args.warmup):
         step(ctx)
@@ -371,6 +374,40 @@ def main():
                  "value": total_cells / (pms * 1e-3), "series_per_s": S / (pms * 1e-3),
                  "ms_per_step": pms, "steps": n_plain}
         pctx.close()
+
+    # the same batched schedule with the full radix selection: what the
+    # learned bracket gains on this workload
+    radix = None
+    if not args.no_radix and form != "plain" and have_model:
+        rctx = make_ctx(rqa.RQA_SCHED_BATCHED)  # radix select
+        rqa.rqa_set_timing(rctx, True)
+        step(rctx)
+        stream.synchronize()
+        n_rad = max(1, min(3, args.steps))
+        rms, rph = 0.0, np.zeros(6, dtype=np.float64)
+        for i in range(n_rad):
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(rctx)
+            e1.record(stream)
+            stream.synchronize()
+            rms += e0.elapsed_time(e1)
+            rph += rqa.rqa_phase_times(rctx)
+        rms /= n_rad
+        rph /= n_rad
+        if rqa.rqa_status(rctx):
+            raise SystemExit("device error in the radix form")
+        rms = max_over_ranks(rms, dist, dev)
+        radix = {"form": "batched, full radix selection (no network)",
+                 "value": world * total_cells / (rms * 1e-3), "series_per_s": world * S / (rms * 1e-3),
+                 "ms_per_step": rms, "steps": n_rad,
+                 "phase_ms": {n: round(float(v), 4) for n, v in
+                              zip(["finite check", "coarse round", "middle round", "final round",
+                                   "line pass", "finalize"], rph)},
+                 "learned_over_radix_series_per_s": (world * S / (ms_max * 1e-3)) / (world * S / (rms * 1e-3))}
+        rctx.close()
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
@@ -448,8 +485,9 @@ def main():
             "config": {"workload": args.workload, "desc": workload_desc(args.workload),
                        "form": f"{form} + radix select" if not have_model else f"{form} + learned bracket",
                        "series": S, "cells_per_step": total_cells, "l2": "flushed between steps",
-                       "line_tile": tuned_tile,
-                       "line_tile_from": "--tile" if args.tile else "rqa_autotune",
+                       "line_tuning": {k: tuned[k] for k in ("tile", "unit_bands", "line_ctas")},
+                       "line_tuning_from": ("--tile + " if args.tile else "") +
+                                           ("tuning cache" if tuned["cached"] else "rqa_autotune"),
                        "parallelism": f"replicas x{world} (series-independent)"},
             "series_per_s": series_per_s,
             "phase_ms": {n: round(float(v), 4) for n, v in zip(names, phase)},
@@ -461,6 +499,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "plain": plain,
+            "radix": radix,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -52,7 +52,7 @@
 extern "C" {
 #endif
 
-#define RQA_ABI_VERSION 1
+#define RQA_ABI_VERSION 2
 #define RQA_K_MAX 127         /* thresholds per series and call */
 #define RQA_M_MAX 16          /* embedding dimension */
 #define RQA_LMIN_MAX 8        /* entries of the lmin list of rqa_det_avg */
@@ -168,12 +168,35 @@ uint64_t rqa_kernel_launches(rqa_ctx *ctx);
 /* Graph replays of rqa_det_avg since the context was created. */
 uint64_t rqa_graph_replays(rqa_ctx *ctx);
 
-/* Line-pass tuning: times the line pass over (a prefix of) the batch for each
- * supported register window (cfg.tile) with the thresholds of rr_num/rr_den,
- * keeps the fastest in the context (used while cfg.tile was 0) and returns
- * it in *tile (host pointer, may be NULL).  Synchronises the stream. */
+/* Schedule knobs of the line pass.  Every setting gives the same results;
+ * only the time differs. */
+typedef struct {
+    int tile;       /* diagonals per register window of the cell phase: 8, 16 or 32
+                       (0 = the default, 16; 8 and 32 only for the embeddings
+                       that cfg.tile lists) */
+    int unit_bands; /* bands of 32 diagonals per work unit a warp takes from the
+                       queue (0 = planned from the batch: about eight units per
+                       resident warp, 1..64 otherwise; capped so a unit stays
+                       under 2^33 cells) */
+    int line_ctas;  /* persistent CTAs of the line pass per SM (0 = as many as
+                       fit, else 1..8) */
+    float ms;       /* rqa_autotune: the line-pass time of the chosen knobs on
+                       the probe, in ms (output only) */
+} rqa_tuning;
+
+/* Line-pass tuning: times the line pass over (a prefix of, at most ~2*10^10
+ * cells of) the batch with the thresholds of rr_num/rr_den, first over the
+ * register windows, then the unit size (half, planned, twice) and the CTAs per
+ * SM (all that fit, or six), each step keeping the fastest; stores the choice
+ * in the context and returns it in *out (host, may be NULL).  A context
+ * created with cfg.tile != 0 keeps that window.  Synchronises the stream. */
 int rqa_autotune(rqa_ctx *ctx, const rqa_batch *batch, const int32_t *rr_num, int32_t rr_den,
-                 int32_t K, int *tile);
+                 int32_t K, rqa_tuning *out);
+
+/* Set (e.g. from a cache of earlier rqa_autotune results) or read the
+ * context's line-pass knobs; RQA_ERR_INVALID_ARG for values out of range. */
+int rqa_set_tuning(rqa_ctx *ctx, const rqa_tuning *t);
+int rqa_get_tuning(rqa_ctx *ctx, rqa_tuning *t);
 
 /* ---- host helpers (no GPU needed) -------------------------------------- */
 

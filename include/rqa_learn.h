@@ -66,6 +66,27 @@ int rqa_mlp_backward(rqa_ctx *ctx, const float *params, const float *X, const fl
 int rqa_adam_step(rqa_ctx *ctx, float *params, const float *grads, float *m, float *v,
                   int64_t n, int32_t t, float lr, float beta1, float beta2, float eps);
 
+/* Training data and validation of the network, on the device:
+ *   rqa_log_labels    T[s][k] = ln(max(eps[s][k], 2^-126)) - centre[s]
+ *                     (eps, T: S x K; centre: S), the targets of the network
+ *                     in the centred log scale of rqa_sketch's features.
+ *   rqa_bracket_eval  over B rows of outputs Y (B x 2K, the ends lo_k, hi_k)
+ *                     and targets T (B x K): loss_sum = summed pinball loss of
+ *                     the 2BK outputs (lower ends at tau_lo, upper at tau_hi;
+ *                     divide by 2BK for the mean of rqa_mlp_backward),
+ *                     inside = targets with lo - margin <= T <= hi + margin,
+ *                     width_sum = summed (hi + margin) - (lo - margin); the
+ *                     three outputs are device scalars (double, uint64, double).
+ *   rqa_gather_rows   dst row r = src row idx[r] (rows of `width` floats, idx
+ *                     device int64, n rows): a minibatch gather. */
+int rqa_log_labels(rqa_ctx *ctx, const float *eps, const float *centre, int32_t S, int32_t K,
+                   float *T);
+int rqa_bracket_eval(rqa_ctx *ctx, const float *Y, const float *T, int32_t B, int32_t K,
+                     float tau_lo, float tau_hi, float margin, double *loss_sum,
+                     uint64_t *inside, double *width_sum);
+int rqa_gather_rows(rqa_ctx *ctx, const float *src, const int64_t *idx, int32_t n, int32_t width,
+                    float *dst);
+
 /* Install a trained network in the context (params copied, device pointer)
  * and the widening margin added to both ends of every interval (in ln units).
  * params == NULL removes the model.  With a model, RQA_SELECT_AUTO uses the

@@ -20,9 +20,9 @@ from .abi import (  # noqa: F401
     rqa_target_counts_loi,
     rqa_set_timing, rqa_phase_times, rqa_kernel_launches,
     rqa_sketch, rqa_mlp_forward, rqa_mlp_backward, rqa_adam_step, rqa_set_bracket_model,
-    rqa_set_bracket_domain, rqa_bracket_stats, RQA_MLP_PARAMS, RQA_MLP_ACTS, RQA_MLP_OUT,
+    rqa_set_bracket_domain, rqa_bracket_stats, rqa_log_labels, rqa_bracket_eval, rqa_gather_rows, RQA_MLP_PARAMS, RQA_MLP_ACTS, RQA_MLP_OUT,
     rqa_eps_for_rr_noalloc, RQA_NOALLOC_MAX_SERIES, RQA_NOALLOC_NE_MAX, RQA_NOALLOC_K_MAX,
-    rqa_graph_replays, rqa_autotune, RQA_FLAG_NO_GRAPHS, RQA_FLAG_LOI, rqa_line_measures,
+    rqa_graph_replays, rqa_autotune, rqa_set_tuning, rqa_get_tuning, RQA_FLAG_NO_GRAPHS, RQA_FLAG_LOI, rqa_line_measures,
     rqa_vline_hist, rqa_lam_tt, rqa_eps_approx,
     RQA_SCHED_BATCHED, RQA_SCHED_PER_SERIES, RQA_SELECT_AUTO, RQA_SELECT_BRACKET,
     RQA_SELECT_RADIX, RQA_K_MAX, RQA_LMIN_MAX, RQA_FEATURES,

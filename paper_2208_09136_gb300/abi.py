@@ -83,6 +83,8 @@ _SIGS = {
     "rqa_lam_tt": ([c_vp, ctypes.POINTER(_Batch), c_i32, c_vp, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp,
                     c_vp], c_int),
     "rqa_autotune": ([c_vp, ctypes.POINTER(_Batch), c_vp, c_i32, c_i32, c_vp], c_int),
+    "rqa_set_tuning": ([c_vp, c_vp], c_int),
+    "rqa_get_tuning": ([c_vp, c_vp], c_int),
     "rqa_line_hist": ([c_vp, ctypes.POINTER(_Batch), c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp],
                       c_int),
     "rqa_sketch": ([c_vp, ctypes.POINTER(_Batch), c_u64, c_vp, c_vp, c_vp], c_int),
@@ -93,6 +95,10 @@ _SIGS = {
                        ctypes.c_float, ctypes.c_float], c_int),
     "rqa_set_bracket_model": ([c_vp, c_vp, ctypes.c_float], c_int),
     "rqa_set_bracket_domain": ([c_vp, c_vp, c_vp, c_i32], c_int),
+    "rqa_log_labels": ([c_vp, c_vp, c_vp, c_i32, c_i32, c_vp], c_int),
+    "rqa_bracket_eval": ([c_vp, c_vp, c_vp, c_i32, c_i32, ctypes.c_float, ctypes.c_float,
+                          ctypes.c_float, c_vp, c_vp, c_vp], c_int),
+    "rqa_gather_rows": ([c_vp, c_vp, c_vp, c_i32, c_i32, c_vp], c_int),
     "rqa_bracket_stats": ([c_vp, c_vp, c_vp], c_int),
     "rqa_eps_for_rr_noalloc": ([ctypes.POINTER(_Batch), c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp,
                                 c_vp], c_int),
@@ -381,14 +387,34 @@ def rqa_graph_replays(ctx: Context) -> int:
     return int(lib().rqa_graph_replays(ctx.handle))
 
 
-def rqa_autotune(ctx: Context, batch: Batch, rr_num, rr_den: int) -> int:
-    """Pick the fastest line-pass register window for this batch; returns it."""
+class _Tuning(ctypes.Structure):
+    _fields_ = [("tile", c_int), ("unit_bands", c_int), ("line_ctas", c_int), ("ms", ctypes.c_float)]
+
+
+def _tuning_dict(t: "_Tuning") -> dict:
+    return {"tile": t.tile, "unit_bands": t.unit_bands, "line_ctas": t.line_ctas, "ms": float(t.ms)}
+
+
+def rqa_autotune(ctx: Context, batch: Batch, rr_num, rr_den: int) -> dict:
+    """Time the line pass's knobs on (a prefix of) this batch and keep the
+    fastest in the context; returns them as a dict."""
     rr = np.ascontiguousarray(rr_num, dtype=np.int32)
     b = batch._c()
-    tile = c_int()
+    t = _Tuning()
     _check(lib().rqa_autotune(ctx.handle, ctypes.byref(b), _np_ptr(rr), int(rr_den), len(rr),
-                              ctypes.byref(tile)), "rqa_autotune")
-    return tile.value
+                              ctypes.byref(t)), "rqa_autotune")
+    return _tuning_dict(t)
+
+
+def rqa_set_tuning(ctx: Context, tile: int = 0, unit_bands: int = 0, line_ctas: int = 0):
+    t = _Tuning(int(tile), int(unit_bands), int(line_ctas), 0.0)
+    _check(lib().rqa_set_tuning(ctx.handle, ctypes.byref(t)), "rqa_set_tuning")
+
+
+def rqa_get_tuning(ctx: Context) -> dict:
+    t = _Tuning()
+    _check(lib().rqa_get_tuning(ctx.handle, ctypes.byref(t)), "rqa_get_tuning")
+    return _tuning_dict(t)
 
 
 def rqa_line_hist(ctx: Context, batch: Batch, eps, K: int, hist=None, hist_offsets=None,
@@ -467,6 +493,37 @@ def rqa_set_bracket_domain(ctx: Context, pairs):
     _check(lib().rqa_set_bracket_domain(ctx.handle, _np_ptr(m) if pairs else None,
                                         _np_ptr(tau) if pairs else None, len(pairs)),
            "rqa_set_bracket_domain")
+
+
+def rqa_log_labels(ctx: Context, eps, centre, T_out):
+    """T_out (S x K) = ln(max(eps, 2^-126)) - centre[:, None], on the device."""
+    import torch
+    S, K = int(eps.shape[0]), int(eps.shape[1])
+    _check(lib().rqa_log_labels(ctx.handle, _dev_ptr(eps, torch.float32, S * K, "eps"),
+                                _dev_ptr(centre, torch.float32, S, "centre"), S, K,
+                                _dev_ptr(T_out, torch.float32, S * K, "T_out")), "rqa_log_labels")
+
+
+def rqa_bracket_eval(ctx: Context, Y, T, tau_lo: float, tau_hi: float, margin: float, out):
+    """Summed pinball loss, targets inside the widened intervals and summed
+    width, into out = (float64 scalar, uint64 scalar, float64 scalar) tensors."""
+    import torch
+    B, K = int(T.shape[0]), int(T.shape[1])
+    loss, inside, width = out
+    _check(lib().rqa_bracket_eval(ctx.handle, _dev_ptr(Y, torch.float32, B * 2 * K, "Y"),
+                                  _dev_ptr(T, torch.float32, B * K, "T"), B, K, float(tau_lo),
+                                  float(tau_hi), float(margin), _dev_ptr(loss, torch.float64, 1, "loss"),
+                                  _dev_ptr(inside, torch.uint64, 1, "inside"),
+                                  _dev_ptr(width, torch.float64, 1, "width")), "rqa_bracket_eval")
+
+
+def rqa_gather_rows(ctx: Context, src, idx, dst):
+    """dst[r] = src[idx[r]] for rows of src.shape[1] floats (idx: device int64)."""
+    import torch
+    n, width = int(idx.shape[0]), int(src.shape[1])
+    _check(lib().rqa_gather_rows(ctx.handle, _dev_ptr(src, torch.float32, None, "src"),
+                                 _dev_ptr(idx, torch.int64, n, "idx"), n, width,
+                                 _dev_ptr(dst, torch.float32, n * width, "dst")), "rqa_gather_rows")
 
 
 def rqa_bracket_stats(ctx: Context):

@@ -102,30 +102,31 @@ def init_params(seed: int = 0) -> np.ndarray:
 
 
 def make_dataset(specs, device: int = 0, chunk: int = 2000, seed: int = 1):
-    """Sketch features X (n x 131) and targets T = ln(eps_k) - c (n x 20), on
-    the GPU, for the series of the given specs."""
+    """Sketch features X (n x 131) and targets T = ln(max(eps_k, 2^-126)) - c
+    (n x 20), on the GPU, for the series of the given specs: exact thresholds
+    by rqa_eps_for_rr, features by rqa_sketch, labels by rqa_log_labels."""
     import torch
     from synth.series import _make_many
     ctx = abi.Context(device=device, select=abi.RQA_SELECT_RADIX)
-    Xs, Ts = [], []
-    for a in range(0, len(specs), chunk):
+    dev = f"cuda:{device}"
+    n = len(specs)
+    X = torch.empty((n, 131), dtype=torch.float32, device=dev)
+    T = torch.empty((n, 20), dtype=torch.float32, device=dev)
+    for a in range(0, n, chunk):
         part = specs[a:a + chunk]
         ys = _make_many(part, cache=False)
         batch = abi.Batch.from_numpy(ys, [sp.m for sp in part], [sp.tau for sp in part], device)
         S = batch.n_series
-        eps = torch.empty((S, 20), dtype=torch.float32, device=f"cuda:{device}")
+        eps = torch.empty((S, 20), dtype=torch.float32, device=dev)
         abi.rqa_eps_for_rr(ctx, batch, RR, 100, eps)
-        feats = torch.empty((S, 131), dtype=torch.float32, device=f"cuda:{device}")
-        centre = torch.empty(S, dtype=torch.float32, device=f"cuda:{device}")
-        abi.rqa_sketch(ctx, batch, seed, feats, centre)
+        centre = torch.empty(S, dtype=torch.float32, device=dev)
+        abi.rqa_sketch(ctx, batch, seed, X[a:a + S], centre)
+        abi.rqa_log_labels(ctx, eps, centre, T[a:a + S])
         code = abi.rqa_status(ctx)
         if code:
             raise RuntimeError(abi.rqa_error_string(code))
-        T = torch.log(torch.clamp(eps, min=TINY)) - centre[:, None]
-        Xs.append(feats)
-        Ts.append(T)
     ctx.close()
-    return torch.cat(Xs), torch.cat(Ts)
+    return X, T
 
 
 def train(workload: str = "train-20000", epochs: int = 60, batch_size: int = 256,
@@ -154,6 +155,12 @@ def train(workload: str = "train-20000", epochs: int = 60, batch_size: int = 256
     B = batch_size
     Y = torch.empty((B, 40), dtype=torch.float32, device=dev)
     acts = torch.empty((B, 512), dtype=torch.float32, device=dev)
+    xb = torch.empty((B, 131), dtype=torch.float32, device=dev)
+    tb = torch.empty((B, 20), dtype=torch.float32, device=dev)
+    Xv = torch.empty((n_val, 131), dtype=torch.float32, device=dev)
+    Tv = torch.empty((n_val, 20), dtype=torch.float32, device=dev)
+    abi.rqa_gather_rows(ctx, X, val_idx, Xv)
+    abi.rqa_gather_rows(ctx, T, val_idx, Tv)
     step = 0
     steps_per_epoch = len(tr_idx) // B
     total = epochs * steps_per_epoch
@@ -163,8 +170,8 @@ def train(workload: str = "train-20000", epochs: int = 60, batch_size: int = 256
         ep_loss = 0.0
         for i in range(steps_per_epoch):
             idx = order[i * B:(i + 1) * B]
-            xb = X.index_select(0, idx).contiguous()
-            tb = T.index_select(0, idx).contiguous()
+            abi.rqa_gather_rows(ctx, X, idx, xb)
+            abi.rqa_gather_rows(ctx, T, idx, tb)
             abi.rqa_mlp_forward(ctx, params, xb, Y, acts)
             abi.rqa_mlp_backward(ctx, params, xb, acts, Y, tb, tau_lo, tau_hi, grads, loss)
             step += 1
@@ -172,8 +179,7 @@ def train(workload: str = "train-20000", epochs: int = 60, batch_size: int = 256
             abi.rqa_adam_step(ctx, params, grads, m, v, step, cur_lr)
             if i % 16 == 0:
                 ep_loss += float(loss.item())
-        vl = evaluate(ctx, params, X.index_select(0, val_idx).contiguous(),
-                      T.index_select(0, val_idx).contiguous(), tau_lo, tau_hi)
+        vl = evaluate(ctx, params, Xv, Tv, tau_lo, tau_hi)
         hist.append(vl)
         if ep % 5 == 0 or ep == epochs - 1:
             log(f"epoch {ep:3d} val loss {vl['loss']:.5f} cover {vl['cover']:.4f} "
@@ -185,18 +191,20 @@ def train(workload: str = "train-20000", epochs: int = 60, batch_size: int = 256
 
 
 def evaluate(ctx, params, X, T, tau_lo, tau_hi, margin: float = 0.0):
-    """Validation loss, fraction of targets inside [lo - margin, hi + margin]
-    and the mean interval width (ln units)."""
+    """Validation loss (mean pinball loss of the 40 outputs), fraction of
+    targets inside [lo - margin, hi + margin] and the mean widened interval
+    width (ln units), all computed by rqa_bracket_eval."""
     import torch
     n = X.shape[0]
     Y = torch.empty((n, 40), dtype=torch.float32, device=X.device)
     abi.rqa_mlp_forward(ctx, params, X, Y)
-    lo, hi = Y[:, 0::2] - margin, Y[:, 1::2] + margin
-    r_lo, r_hi = T - Y[:, 0::2], T - Y[:, 1::2]
-    loss = (torch.where(r_lo >= 0, tau_lo * r_lo, (tau_lo - 1) * r_lo).mean() +
-            torch.where(r_hi >= 0, tau_hi * r_hi, (tau_hi - 1) * r_hi).mean()) / 2
-    cover = ((T >= lo) & (T <= hi)).float().mean()
-    return {"loss": float(loss), "cover": float(cover), "width": float((hi - lo).mean())}
+    out = (torch.empty(1, dtype=torch.float64, device=X.device),
+           torch.empty(1, dtype=torch.uint64, device=X.device),
+           torch.empty(1, dtype=torch.float64, device=X.device))
+    abi.rqa_bracket_eval(ctx, Y, T, tau_lo, tau_hi, margin, out)
+    loss, inside, width = (float(v.cpu().item()) for v in out)
+    m = n * T.shape[1]
+    return {"loss": loss / (2 * m), "cover": inside / m, "width": width / m}
 
 
 def main(argv=None):

@@ -54,6 +54,9 @@ struct rqa_ctx {
     int select = RQA_SELECT_AUTO;
     int band = 16;          // diagonals per band of the counting rounds
     int line_tile = 0;      // diagonals per register window of the line pass (0 = default)
+    int unit_bands = 0;     // bands per line-pass work unit (0 = planned)
+    int line_ctas = 0;      // persistent line-pass CTAs per SM (0 = all that fit)
+    float tuned_ms = 0.f;   // line-pass time of the last rqa_autotune choice
     bool tile_fixed = false;  // the caller chose the tile: rqa_autotune keeps it
     bool loi = false;         // RQA_FLAG_LOI: rates and DET over the whole matrix
     int bpsm = 0;
@@ -307,7 +310,8 @@ int make_plan(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_
     for (int s = 0; s < S; ++s) pl.ne_max = std::max(pl.ne_max, pl.sd[s].ne);
     const int64_t chunk_cap = std::max<int64_t>(1, ((int64_t)1 << 28) / std::max(pl.ne_max, 1));
     auto chunk_for = [&](int64_t bands) {
-        const int64_t ch = std::max<int64_t>(1, std::min<int64_t>(64, bands / (n_warps * 8)));
+        int64_t ch = std::max<int64_t>(1, std::min<int64_t>(64, bands / (n_warps * 8)));
+        if (c->unit_bands > 0) ch = c->unit_bands;  // a tuned size
         return (int32_t)std::min(ch, chunk_cap);
     };
     pl.line_tile = c->line_tile ? c->line_tile : LINE_TILE_DEFAULT;
@@ -607,6 +611,7 @@ int run_lines(rqa_ctx *c, const Plan &pl, const float *eps, uint64_t *hist, cons
     a.series = pl.d_sd;
     a.band = c->band;
     a.line_tile = pl.line_tile;
+    a.line_ctas = c->line_ctas;
     a.status = P<int>(c->status);
     unsigned *q = nullptr;
     const int full_grid = persistent_grid(c, (size_t)1 << 30);
@@ -913,7 +918,7 @@ int rqa_det_avg(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t r
         auto put = [&](uint64_t v) { sig.push_back(v); };
         auto ptr = [&](const void *p) { put((uint64_t)(uintptr_t)p); };
         put((uint64_t)pl.S); put((uint64_t)K); put((uint64_t)n_lmin); put((uint64_t)rr_den);
-        put(bracket); put((uint64_t)c->schedule); put((uint64_t)pl.line_tile); put(c->timing);
+        put(bracket); put((uint64_t)c->schedule); put((uint64_t)pl.line_tile); put((uint64_t)c->unit_bands); put((uint64_t)c->line_ctas); put(c->timing);
         for (int s = 0; s < pl.S; ++s) put(pl.dom[s]);
         put(c->loi);
         uint32_t mb;
@@ -1179,16 +1184,34 @@ uint64_t rqa_kernel_launches(rqa_ctx *c) { return c ? c->launches : 0; }
 
 uint64_t rqa_graph_replays(rqa_ctx *c) { return c ? c->graph_replays : 0; }
 
+int rqa_set_tuning(rqa_ctx *c, const rqa_tuning *t)
+{
+    if (!c || !t) return RQA_ERR_INVALID_ARG;
+    if (t->tile != 0 && t->tile != 8 && t->tile != 16 && t->tile != 32) return RQA_ERR_INVALID_ARG;
+    if (t->unit_bands < 0 || t->unit_bands > 64 || t->line_ctas < 0 || t->line_ctas > 8)
+        return RQA_ERR_INVALID_ARG;
+    c->line_tile = t->tile;
+    c->unit_bands = t->unit_bands;
+    c->line_ctas = t->line_ctas;
+    return RQA_OK;
+}
+
+int rqa_get_tuning(rqa_ctx *c, rqa_tuning *t)
+{
+    if (!c || !t) return RQA_ERR_INVALID_ARG;
+    t->tile = c->line_tile ? c->line_tile : LINE_TILE_DEFAULT;
+    t->unit_bands = c->unit_bands;
+    t->line_ctas = c->line_ctas;
+    t->ms = c->tuned_ms;
+    return RQA_OK;
+}
+
 int rqa_autotune(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_den, int32_t K,
-                 int *band)
+                 rqa_tuning *out)
 {
     if (!c) return RQA_ERR_INVALID_ARG;
     if (int rc = validate_batch(b)) return rc;
     if (int rc = validate_rr(rr_num, rr_den, K)) return rc;
-    if (c->tile_fixed) {
-        if (band) *band = c->line_tile;
-        return RQA_OK;
-    }
     cudaSetDevice(c->device);
     // sample: the longest prefix of the batch under ~2e10 cells (at least one series)
     rqa_batch sb = *b;
@@ -1201,8 +1224,15 @@ int rqa_autotune(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t 
         cells += pc;
     }
     sb.n_series = j;
+    const int saved[3] = {c->line_tile, c->unit_bands, c->line_ctas};
+    c->unit_bands = 0;  // the planned unit size, for the probe's plan
+    c->line_ctas = 0;
     Plan probe;
-    if (int rc = make_plan(c, &sb, nullptr, 0, K, probe)) return rc;
+    const int rcp = make_plan(c, &sb, nullptr, 0, K, probe);
+    c->unit_bands = saved[1];
+    c->line_ctas = saved[2];
+    if (rcp) return rcp;
+    if (probe.ne_max > LINE_NE_MAX) return RQA_ERR_CAPACITY;
     if (int rc = ensure(c->eps_tmp, (size_t)sb.n_series * K * 4)) return rc;
     float *eps = P<float>(c->eps_tmp);
     const int saved_select = c->select;
@@ -1213,13 +1243,10 @@ int rqa_autotune(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t 
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return check_cuda(cudaGetLastError());
-    const int saved_band = c->line_tile;
-    int best = LINE_TILE_DEFAULT;
-    float best_ms = 3.4e38f;
-    const int cand[3] = {8, 16, 32};
-    for (int ci = 0; ci < 3 && rc == RQA_OK; ++ci) {
-        if (!lines_tile_ok(probe.mt, cand[ci])) continue;
-        c->line_tile = cand[ci];
+    c->unit_bands = 0;
+    c->line_ctas = 0;
+    // the line pass over the probe with the context's current knobs, best of two
+    auto time_lines = [&](float *best) {
         float t_min = 3.4e38f;
         for (int rep = 0; rep < 2 && rc == RQA_OK; ++rep) {
             cudaEventRecord(e0, c->stream);
@@ -1229,16 +1256,64 @@ int rqa_autotune(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t 
             float ms = 0.f;
             if (rc == RQA_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) t_min = std::min(t_min, ms);
         }
-        if (t_min < best_ms) {
-            best_ms = t_min;
-            best = cand[ci];
+        *best = t_min;
+    };
+    float best_ms = 3.4e38f;
+    // 1. register window (kept when the caller fixed it)
+    int best_tile = c->line_tile ? c->line_tile : LINE_TILE_DEFAULT;
+    if (!c->tile_fixed) {
+        const int cand[3] = {8, 16, 32};
+        for (int ci = 0; ci < 3 && rc == RQA_OK; ++ci) {
+            if (!lines_tile_ok(probe.mt, cand[ci])) continue;
+            c->line_tile = cand[ci];
+            float ms = 0.f;
+            time_lines(&ms);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_tile = cand[ci];
+            }
         }
     }
+    c->line_tile = best_tile;
+    if (best_ms == 3.4e38f && rc == RQA_OK) time_lines(&best_ms);
+    // 2. bands per work unit: half and twice the planned size
+    int best_units = 0;
+    const int planned = probe.chunk;
+    const int ucand[2] = {std::max(1, planned / 2), std::min(64, planned * 2)};
+    for (int ci = 0; ci < 2 && rc == RQA_OK; ++ci) {
+        if (ucand[ci] == planned) continue;
+        c->unit_bands = ucand[ci];
+        float ms = 0.f;
+        time_lines(&ms);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_units = ucand[ci];
+        }
+    }
+    c->unit_bands = best_units;
+    // 3. CTAs per SM: all that fit, or six
+    int best_ctas = 0;
+    if (rc == RQA_OK) {
+        c->line_ctas = 6;
+        float ms = 0.f;
+        time_lines(&ms);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_ctas = 6;
+        }
+    }
+    c->line_ctas = best_ctas;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->line_tile = rc == RQA_OK ? best : saved_band;
-    if (band) *band = c->line_tile;
-    return rc;
+    if (rc != RQA_OK) {
+        c->line_tile = saved[0];
+        c->unit_bands = saved[1];
+        c->line_ctas = saved[2];
+        return rc;
+    }
+    c->tuned_ms = best_ms;
+    if (out) rqa_get_tuning(c, out);
+    return RQA_OK;
 }
 
 // ---------------------------------------------------------- learned bracket
@@ -1303,6 +1378,33 @@ int rqa_set_bracket_model(rqa_ctx *c, const float *params, float margin)
     c->has_model = true;
     c->margin = margin;
     return RQA_OK;
+}
+
+int rqa_log_labels(rqa_ctx *c, const float *eps, const float *centre, int32_t S, int32_t K, float *T)
+{
+    if (!c || !eps || !centre || !T || S < 1 || K < 1) return RQA_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    return launched(c, launch_log_labels(eps, centre, S, K, T, c->stream));
+}
+
+int rqa_bracket_eval(rqa_ctx *c, const float *Y, const float *T, int32_t B, int32_t K, float tau_lo,
+                     float tau_hi, float margin, double *loss_sum, uint64_t *inside, double *width_sum)
+{
+    if (!c || !Y || !T || !loss_sum || !inside || !width_sum || B < 1 || K < 1)
+        return RQA_ERR_INVALID_ARG;
+    if (!(tau_lo > 0.f && tau_lo < 1.f && tau_hi > 0.f && tau_hi < 1.f && margin >= 0.f))
+        return RQA_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    return launched(c, launch_bracket_eval(Y, T, B, K, tau_lo, tau_hi, margin, loss_sum,
+                                           reinterpret_cast<unsigned long long *>(inside), width_sum,
+                                           c->stream));
+}
+
+int rqa_gather_rows(rqa_ctx *c, const float *src, const int64_t *idx, int32_t n, int32_t width, float *dst)
+{
+    if (!c || !src || !idx || !dst || n < 1 || width < 1) return RQA_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    return launched(c, launch_gather_rows(src, idx, n, width, dst, c->stream));
 }
 
 int rqa_set_bracket_domain(rqa_ctx *c, const int32_t *m, const int32_t *tau, int32_t n)

@@ -274,6 +274,95 @@ cudaError_t adam_step(float *p, const float *g, float *m, float *v, int64_t n, i
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ training data
+// Labels of the network: T[s][k] = ln(max(eps[s][k], 2^-126)) - c[s], the
+// thresholds in the centred log scale of the sketch features.
+__global__ void k_log_labels(const float *__restrict__ eps, const float *__restrict__ centre, int S,
+                             int K, float *__restrict__ T)
+{
+    const int64_t n = (int64_t)S * K;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        T[e] = logf(fmaxf(eps[e], 0x1p-126f)) - centre[e / K];
+}
+
+cudaError_t launch_log_labels(const float *eps, const float *centre, int S, int K, float *T,
+                              cudaStream_t st)
+{
+    const int64_t n = (int64_t)S * K;
+    k_log_labels<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, st>>>(eps, centre, S, K, T);
+    return cudaGetLastError();
+}
+
+// Validation of a bracket network over B rows: the summed pinball loss of the
+// 2K outputs (lower ends at tau_lo, upper at tau_hi), the targets inside
+// [lo - margin, hi + margin] and the summed width hi - lo + 2 margin.
+__global__ void k_bracket_eval(const float *__restrict__ Y, const float *__restrict__ T, int B,
+                               int K, float tau_lo, float tau_hi, float margin, double *loss_sum,
+                               unsigned long long *inside, double *width_sum)
+{
+    double l = 0.0, w = 0.0;
+    unsigned long long in = 0;
+    const int64_t n = (int64_t)B * K;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = e / K;
+        const int k = (int)(e % K);
+        const float t = T[e];
+        const float lo = Y[b * 2 * K + 2 * k], hi = Y[b * 2 * K + 2 * k + 1];
+        const float rl = t - lo, rh = t - hi;
+        l += (double)((rl >= 0.f) ? tau_lo * rl : (tau_lo - 1.f) * rl);
+        l += (double)((rh >= 0.f) ? tau_hi * rh : (tau_hi - 1.f) * rh);
+        in += (t >= lo - margin && t <= hi + margin) ? 1ull : 0ull;
+        w += (double)((hi + margin) - (lo - margin));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        l += __shfl_xor_sync(FULL, l, o);
+        w += __shfl_xor_sync(FULL, w, o);
+        in += __shfl_xor_sync(FULL, in, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(loss_sum, l);
+        atomicAdd(width_sum, w);
+        atomicAdd(inside, in);
+    }
+}
+
+cudaError_t launch_bracket_eval(const float *Y, const float *T, int B, int K, float tau_lo,
+                                float tau_hi, float margin, double *loss_sum,
+                                unsigned long long *inside, double *width_sum, cudaStream_t st)
+{
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(loss_sum, 0, sizeof(double), st))) return e;
+    if ((e = cudaMemsetAsync(width_sum, 0, sizeof(double), st))) return e;
+    if ((e = cudaMemsetAsync(inside, 0, sizeof(unsigned long long), st))) return e;
+    const int64_t n = (int64_t)B * K;
+    k_bracket_eval<<<(int)std::min<int64_t>((n + 255) / 256, 512), 256, 0, st>>>(
+        Y, T, B, K, tau_lo, tau_hi, margin, loss_sum, inside, width_sum);
+    return cudaGetLastError();
+}
+
+// dst row r = src row idx[r], rows of `width` floats (a minibatch gather).
+__global__ void k_gather_rows(const float *__restrict__ src, const int64_t *__restrict__ idx, int n,
+                              int width, float *__restrict__ dst)
+{
+    const int64_t total = (int64_t)n * width;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / width;
+        dst[e] = src[idx[r] * width + (e - r * width)];
+    }
+}
+
+cudaError_t launch_gather_rows(const float *src, const int64_t *idx, int n, int width, float *dst,
+                               cudaStream_t st)
+{
+    const int64_t total = (int64_t)n * width;
+    k_gather_rows<<<(int)std::min<int64_t>((total + 255) / 256, 2048), 256, 0, st>>>(src, idx, n, width, dst);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ bracket
 // Coarse buckets to split in the first counting round.  Per target the
 // interval runs from the bucket of exp(c + lo - margin) to that of

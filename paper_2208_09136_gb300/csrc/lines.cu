@@ -1,6 +1,8 @@
 // Line pass launches: the kernel variant for the batch's embedding and the
 // register window, on a persistent grid (the kernel is in lines_kernel.cuh,
 // its instantiations in lines_*.cu).
+#include <algorithm>
+
 #include "lines_kernel.cuh"
 
 namespace rqa {
@@ -46,6 +48,7 @@ static cudaError_t launch_lines_v(const CellArgs &a, const LineBufs &lb, int K, 
     if (e != cudaSuccess) return e;
     grid *= WARPS / LWARPS;  // the caller counts CTAs of WARPS warps
     grid = persistent_cap(reinterpret_cast<const void *>(kern), smem, grid, LTHREADS);
+    if (a.line_ctas > 0) grid = std::min(grid, sm_count_current() * a.line_ctas);
     kern<<<grid, LTHREADS, smem, st>>>(a, lb, K);
     return cudaGetLastError();
 }

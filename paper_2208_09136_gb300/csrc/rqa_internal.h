@@ -86,6 +86,7 @@ struct CellArgs {
     int32_t n_pos;
     int32_t chunk;           // bands per unit
     int32_t line_tile;       // diagonals per register window of the line pass (8, 16 or 32)
+    int32_t line_ctas;       // persistent CTAs of the line pass per SM (0: as many as fit)
     int64_t n_units;
     unsigned int *queue;   // ticket counter (64-bit aligned), zeroed before launch
     int *status;

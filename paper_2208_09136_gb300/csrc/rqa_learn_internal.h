@@ -27,6 +27,13 @@ cudaError_t mlp_backward(const float *params, const float *X, const float *acts,
                          float *loss, float *scratch, cudaStream_t st);
 cudaError_t adam_step(float *p, const float *g, float *m, float *v, int64_t n, int t, float lr,
                       float b1, float b2, float eps, cudaStream_t st);
+cudaError_t launch_log_labels(const float *eps, const float *centre, int S, int K, float *T,
+                              cudaStream_t st);
+cudaError_t launch_bracket_eval(const float *Y, const float *T, int B, int K, float tau_lo,
+                                float tau_hi, float margin, double *loss_sum,
+                                unsigned long long *inside, double *width_sum, cudaStream_t st);
+cudaError_t launch_gather_rows(const float *src, const int64_t *idx, int n, int width, float *dst,
+                               cudaStream_t st);
 // also writes range[2s], range[2s+1]: the keys of the split buckets' span.
 // dom[s] == 0: series s is not bracketed (no split bucket, empty range).
 cudaError_t launch_bracket(const float *Y, const float *centre, float margin, int S, int K,

@@ -99,16 +99,20 @@ def test_short_series_against_oracle(full_run):
 
 
 def test_long_series_sampled_against_oracle(full_run):
-    """One long series per signal type: thresholds proven exact by the
-    oracle's counting certificate #{d < eps} < T <= #{d <= eps} (and C_k equal
-    to the oracle's count); the first of them also through the oracle's full
-    diagonal scan (histograms, stencil, L_max)."""
+    """One long series per signal type and SNR (24 of the 96): thresholds
+    proven exact by the oracle's counting certificate #{d < eps} < T <=
+    #{d <= eps} (and C_k equal to the oracle's count); the 0 dB sine series
+    also through the oracle's full diagonal scan (histograms, stencil,
+    L_max)."""
     from oracle import c_oracle as CO
     w, flat, offsets, m, tau, res, _ = full_run
+    snrs = sorted({sp.snr_db for sp in w.specs if sp.n == 100_000})
+    assert len(snrs) == 8
     picks = []
     for kind in ("sine", "logistic", "lorenz"):
-        picks.append(next(i for i, sp in enumerate(w.specs) if sp.kind == kind and sp.n == 100_000
-                          and sp.snr_db == 0.0))
+        for snr in ([0.0] + [v for v in snrs if v != 0.0]):
+            picks.append(next(i for i, sp in enumerate(w.specs) if sp.kind == kind and sp.n == 100_000
+                              and sp.snr_db == snr))
     for idx, s in enumerate(picks):
         y = flat[offsets[s]:offsets[s + 1]]
         ne = len(y) - (int(m[s]) - 1) * int(tau[s])

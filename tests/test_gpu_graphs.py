@@ -163,14 +163,24 @@ def test_autotune_picks_a_supported_tile_and_stays_exact(rqa_lib):
     ys = _series(13, [6000, 800, 4000])
     ctx = rqa.Context(stream=stream, select=rqa.RQA_SELECT_RADIX)
     run = _Run(rqa, ctx, ys, 3, 3, stream)
-    tile = rqa.rqa_autotune(ctx, run.batch, RR20, 100)
-    assert tile in (8, 16, 32)
-    assert rqa.rqa_device_info(ctx)["tile"] == tile
+    t = rqa.rqa_autotune(ctx, run.batch, RR20, 100)
+    assert t["tile"] in (8, 16, 32) and 0 <= t["unit_bands"] <= 64 and t["line_ctas"] in (0, 6)
+    assert t["ms"] > 0
+    assert rqa.rqa_device_info(ctx)["tile"] == t["tile"]
+    assert {k: v for k, v in rqa.rqa_get_tuning(ctx).items() if k != "ms"} == \
+        {k: v for k, v in t.items() if k != "ms"}
     res = run.call()
     _against_oracle(res, ys, 3, 3)
+    # every knob setting gives the same results: the smallest units, few CTAs
+    rqa.rqa_set_tuning(ctx, tile=8, unit_bands=1, line_ctas=1)
+    _against_oracle(run.call(), ys, 3, 3)
+    rqa.rqa_set_tuning(ctx, tile=32, unit_bands=64, line_ctas=8)
+    _against_oracle(run.call(), ys, 3, 3)
+    with pytest.raises(rqa.RqaError):
+        rqa.rqa_set_tuning(ctx, tile=12)
     # a context created with an explicit tile keeps it
     ctx2 = rqa.Context(stream=stream, select=rqa.RQA_SELECT_RADIX, tile=8)
-    assert rqa.rqa_autotune(ctx2, run.batch, RR20, 100) == 8
+    assert rqa.rqa_autotune(ctx2, run.batch, RR20, 100)["tile"] == 8
     ctx.close()
     ctx2.close()
 

@@ -257,3 +257,49 @@ def test_auto_selection_keeps_to_the_training_domain(rqa_lib):
     rqa.eps_for_rr(ctx, rqa.Batch.from_numpy(ys, 1, 1), RR20, 100)
     assert sum(rqa.rqa_bracket_stats(ctx)) == 80
     ctx.close()
+
+
+def test_training_arithmetic_kernels(rqa_lib):
+    """The label, validation and gather kernels the trainer uses, against
+    NumPy: labels ln(max(eps, 2^-126)) - c within FP32 rounding of the
+    logarithm, the inside count exactly (the same FP32 comparisons), the loss
+    and width sums to double rounding, the gather exactly."""
+    import torch
+    rqa = rqa_lib
+    rng = np.random.default_rng(17)
+    ctx = rqa.Context()
+    S, K = 300, 20
+    eps = (np.exp(rng.uniform(-9, 2, (S, K))) * (rng.random((S, K)) > 0.01)).astype(np.float32)
+    centre = rng.uniform(-3, 1, S).astype(np.float32)
+    T = torch.empty((S, K), dtype=torch.float32, device="cuda")
+    rqa.rqa_log_labels(ctx, torch.from_numpy(eps).cuda(), torch.from_numpy(centre).cuda(), T)
+    ref = np.log(np.maximum(eps.astype(np.float64), 2.0 ** -126)) - centre[:, None].astype(np.float64)
+    got = T.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got - ref) <= 4e-7 * np.maximum(1.0, np.abs(ref)))
+    # validation sums over rows of predictions
+    B = 257
+    Y = rng.standard_normal((B, 2 * K)).astype(np.float32)
+    Y[:, 1::2] = Y[:, 0::2] + np.abs(Y[:, 1::2])
+    Tt = rng.standard_normal((B, K)).astype(np.float32)
+    out = (torch.empty(1, dtype=torch.float64, device="cuda"),
+           torch.empty(1, dtype=torch.uint64, device="cuda"),
+           torch.empty(1, dtype=torch.float64, device="cuda"))
+    tl, th, mg = np.float32(0.005), np.float32(0.995), np.float32(0.05)
+    rqa.rqa_bracket_eval(ctx, torch.from_numpy(Y).cuda(), torch.from_numpy(Tt).cuda(), float(tl),
+                         float(th), float(mg), out)
+    loss, inside, width = (v.cpu().item() for v in out)
+    lo, hi = Y[:, 0::2], Y[:, 1::2]
+    rl, rh = Tt - lo, Tt - hi
+    pl = np.where(rl >= 0, tl * rl, (tl - np.float32(1)) * rl).astype(np.float64)
+    ph = np.where(rh >= 0, th * rh, (th - np.float32(1)) * rh).astype(np.float64)
+    assert abs(loss - (pl.sum() + ph.sum())) <= 1e-9 * max(1.0, abs(loss))
+    assert inside == int(((Tt >= lo - mg) & (Tt <= hi + mg)).sum())
+    assert abs(width - ((hi + mg) - (lo - mg)).astype(np.float64).sum()) <= 1e-9 * abs(width)
+    # gather
+    idx = rng.integers(0, S, 77)
+    src = rng.standard_normal((S, 131)).astype(np.float32)
+    dst = torch.empty((77, 131), dtype=torch.float32, device="cuda")
+    rqa.rqa_gather_rows(ctx, torch.from_numpy(src).cuda(), torch.from_numpy(idx).cuda(), dst)
+    assert np.array_equal(dst.cpu().numpy(), src[idx])
+    assert rqa.rqa_status(ctx) == 0
+    ctx.close()
