@@ -8,10 +8,12 @@
 //  cells  lane t holds row i0+t.  For every diagonal j of the band it computes
 //         the distance of cell (i0+t, i0+t+d_lo+j) and its rank
 //         r = #{k : eps_k < d} (one lookup in a bucket table of the
-//         thresholds, or a 5-step search over them); five __ballot_sync calls
-//         publish the bit planes of r over the 32 rows, and one lane stores
-//         them in shared memory.
-//  runs   lane j holds diagonal j.  It reads its five planes and, for every
+//         thresholds, or a 5-step search over them) and stores r as byte
+//         [j][t] of a 32 x 32 rank matrix in shared memory.
+//  runs   lane j holds diagonal j.  It reads row j of the matrix (the ranks of
+//         its 32 cells, two 16-byte loads) and gathers their five bit planes
+//         with masks and multiplies (bit p of four bytes lands in four
+//         adjacent bits of a product); then, for every
 //         threshold k, rebuilds the 32-row recurrence word {t : r_t <= k} (the
 //         borrow out of r - (k+1), two LOP3s).  A line ends at row t-1 where
 //         row t-1 is recurrent and row t is not; copies of the word shifted
@@ -58,9 +60,13 @@ static_assert(LSH > WSH, "lengths WSH+1..LSH go to the global short histogram");
 //   lq    [KT][LD] 8 bytes each: when the word of threshold k of diagonal j
 //         ends lines of length >= 4, their end mask and the run open above
 //         the word; they are measured after the threshold loop (the word
-//         itself is rebuilt there from the row block's planes)
+//         itself is rebuilt there from the row block's planes).  The same
+//         space first holds the row block's rank matrix, [LD][32] bytes (row
+//         j: the ranks of diagonal j's 32 cells), read before any slot is
+//         written.
 //   pl    [LD][4] bit planes 0..3 of the ranks of the current row block (16-byte rows)
-//   pl4   [LD]    bit plane 4
+//   pl4   [LD]    bit plane 4 (both written by lane j for diagonal j, read back
+//                 when the lines of length >= 4 are measured)
 //   epsb  [32]    threshold keys of the current series (padding above every key)
 //   tab   [TMAX]  rank table
 //   hs    [HROW][32] line counts by length, column k for threshold k (a lane
@@ -176,6 +182,7 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
     uint32_t *pl = ws + O_PL, *pl4 = ws + O_PL4, *epsb = ws + O_EPS, *tab = ws + O_TAB;
     uint32_t *hs = ws + O_HS + lane;  // this lane's column: [l * 32], threshold k = lane
     uint2 *lqa = reinterpret_cast<uint2 *>(ws + O_LQ);  // [k * LD + j]
+    unsigned char *rkm = reinterpret_cast<unsigned char *>(ws + O_LQ);  // rank matrix [j][t]
     uint2 *lq = lqa + lane;                               // slots of this lane's diagonal
     // lane k: the bits of k + 1 as masks, for its own recurrence words
     uint32_t kbm[5];
@@ -423,7 +430,6 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
                             if (INTERIOR) tile.load_fast(ys, i, d_lo + jc, sd.tau);
                             else tile.load(ys, sd.n, i, d_lo + jc, rows, sd.tau, sd.m);
                         }
-                        uint32_t g4[4];  // plane 4 of four consecutive diagonals: one store
 #pragma unroll
                         for (int j = 0; j < JC; ++j) {
                             const int col = c_lo + jc + j;   // vertical pass: column
@@ -441,17 +447,7 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
                                 const uint32_t rk = rank_of(key);
                                 r = valid ? rk : 31u;
                             }
-                            const uint32_t B0 = __ballot_sync(FULL, r & 1u);
-                            const uint32_t B1 = __ballot_sync(FULL, r & 2u);
-                            const uint32_t B2 = __ballot_sync(FULL, r & 4u);
-                            const uint32_t B3 = __ballot_sync(FULL, r & 8u);
-                            g4[j & 3] = __ballot_sync(FULL, r & 16u);
-                            if (lane == 0) {
-                                *reinterpret_cast<uint4 *>(pl + (jc + j) * 4) = make_uint4(B0, B1, B2, B3);
-                                if ((j & 3) == 3)
-                                    *reinterpret_cast<uint4 *>(pl4 + jc + j - 3) =
-                                        make_uint4(g4[0], g4[1], g4[2], g4[3]);
-                            }
+                            rkm[(jc + j) * 32 + lane] = (unsigned char)r;
                         }
                     }
                 };
@@ -459,9 +455,26 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
                 // run phase of the same 32 rows: lane j takes diagonal j
                 auto run_phase = [&]() {
                     __syncwarp();
-                    const uint4 q = *reinterpret_cast<const uint4 *>(pl + lane * 4);
-                    const uint32_t B[5] = {q.x, q.y, q.z, q.w, pl4[lane]};
-                    __syncwarp();  // the next block's stores wait for these loads
+                    const uint4 ra = *reinterpret_cast<const uint4 *>(rkm + lane * 32);
+                    const uint4 rb = *reinterpret_cast<const uint4 *>(rkm + lane * 32 + 16);
+                    const uint32_t R[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+                    // bit p of the four ranks of word q (rows 4q..4q+3, one per
+                    // byte): masked, then multiplied so they land in bits 28..31
+                    uint32_t B[5];
+#pragma unroll
+                    for (int p = 0; p < 5; ++p) {
+                        uint32_t b = 0;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const uint32_t v = (R[q] & (0x01010101u << p)) * (0x10204080u >> p);
+                            b |= q < 7 ? (v >> (28 - 4 * q)) & (0xFu << (4 * q)) : v & 0xF0000000u;
+                        }
+                        B[p] = b;
+                    }
+                    // this diagonal's planes, for rebuilding words of long lines
+                    *reinterpret_cast<uint4 *>(pl + lane * 4) = make_uint4(B[0], B[1], B[2], B[3]);
+                    pl4[lane] = B[4];
+                    __syncwarp();  // rank rows read before slots overwrite them
                     uint32_t lmask = 0;  // thresholds whose word ends lines of length >= 4
 #pragma unroll
                     for (int k = 0; k < KT; ++k) {
