@@ -462,8 +462,9 @@ def main():
                 "ncu": None if traffic is None or "issue_active_pct" not in traffic else {
                     "issue_active_pct": traffic["issue_active_pct"],
                     "alu_pipe_pct": traffic["alu_pipe_pct"],
-                    "warp_inst_per_32_cells": round(traffic["warp_instructions"] * 32 / total_cells, 1),
-                    "source": "profiles/traffic.json (one ncu pass of the same kernel on this workload)"},
+                    "warp_inst_per_32_cells": traffic["warp_inst_per_32_cells"],
+                    "source": "profiles/traffic.json: DRAM bytes from one ncu pass of this kernel on this "
+                              "workload; issue, ALU and instructions from " + traffic.get("inst_source", "")},
                 "ops_per_cell": ops_cell,
                 "peak_note": f"{sm} SMs x 128 lanes x {f_max/1e6:.0f} MHz (max SM clock)"}
 
