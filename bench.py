@@ -486,7 +486,7 @@ def main():
             "config": {"workload": args.workload, "desc": workload_desc(args.workload),
                        "form": f"{form} + radix select" if not have_model else f"{form} + learned bracket",
                        "series": S, "cells_per_step": total_cells, "l2": "flushed between steps",
-                       "line_tuning": {k: tuned[k] for k in ("tile", "unit_bands", "line_ctas")},
+                       "line_tuning": {k: tuned[k] for k in ("tile", "unit_bands", "line_ctas", "stage")},
                        "line_tuning_from": ("--tile + " if args.tile else "") +
                                            ("tuning cache" if tuned["cached"] else "rqa_autotune"),
                        "parallelism": f"replicas x{world} (series-independent)"},

@@ -52,7 +52,7 @@
 extern "C" {
 #endif
 
-#define RQA_ABI_VERSION 2
+#define RQA_ABI_VERSION 3
 #define RQA_K_MAX 127         /* thresholds per series and call */
 #define RQA_M_MAX 16          /* embedding dimension */
 #define RQA_LMIN_MAX 8        /* entries of the lmin list of rqa_det_avg */
@@ -180,14 +180,24 @@ typedef struct {
                        under 2^33 cells) */
     int line_ctas;  /* persistent CTAs of the line pass per SM (0 = as many as
                        fit, else 1..8) */
+    int stage;      /* 1: the diagonal pass brings each interior row block's
+                       series values into shared memory with 1-D bulk copies
+                       (cp.async.bulk, completion on an mbarrier, the next
+                       block's copy in flight while the current one computes);
+                       0: every lane reads its window through L1.  Only for
+                       m = 3 with tau = 3 or 1 and windows of 16 or 32
+                       diagonals; ignored elsewhere.  A copy whose barrier does
+                       not complete within a bounded wait sets RQA_ERR_TIMEOUT
+                       and the block is read directly. */
     float ms;       /* rqa_autotune: the line-pass time of the chosen knobs on
                        the probe, in ms (output only) */
 } rqa_tuning;
 
 /* Line-pass tuning: times the line pass over (a prefix of, at most ~2*10^10
  * cells of) the batch with the thresholds of rr_num/rr_den, first over the
- * register windows, then the unit size (half, planned, twice) and the CTAs per
- * SM (all that fit, or six), each step keeping the fastest; stores the choice
+ * register windows, then the unit size (half, planned, twice), the CTAs per
+ * SM (all that fit, or six) and the staging of series windows (off, on where
+ * the variant exists), each step keeping the fastest; stores the choice
  * in the context and returns it in *out (host, may be NULL).  A context
  * created with cfg.tile != 0 keeps that window.  Synchronises the stream. */
 int rqa_autotune(rqa_ctx *ctx, const rqa_batch *batch, const int32_t *rr_num, int32_t rr_den,

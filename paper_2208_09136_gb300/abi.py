@@ -388,11 +388,13 @@ def rqa_graph_replays(ctx: Context) -> int:
 
 
 class _Tuning(ctypes.Structure):
-    _fields_ = [("tile", c_int), ("unit_bands", c_int), ("line_ctas", c_int), ("ms", ctypes.c_float)]
+    _fields_ = [("tile", c_int), ("unit_bands", c_int), ("line_ctas", c_int), ("stage", c_int),
+                ("ms", ctypes.c_float)]
 
 
 def _tuning_dict(t: "_Tuning") -> dict:
-    return {"tile": t.tile, "unit_bands": t.unit_bands, "line_ctas": t.line_ctas, "ms": float(t.ms)}
+    return {"tile": t.tile, "unit_bands": t.unit_bands, "line_ctas": t.line_ctas, "stage": t.stage,
+            "ms": float(t.ms)}
 
 
 def rqa_autotune(ctx: Context, batch: Batch, rr_num, rr_den: int) -> dict:
@@ -406,8 +408,9 @@ def rqa_autotune(ctx: Context, batch: Batch, rr_num, rr_den: int) -> dict:
     return _tuning_dict(t)
 
 
-def rqa_set_tuning(ctx: Context, tile: int = 0, unit_bands: int = 0, line_ctas: int = 0):
-    t = _Tuning(int(tile), int(unit_bands), int(line_ctas), 0.0)
+def rqa_set_tuning(ctx: Context, tile: int = 0, unit_bands: int = 0, line_ctas: int = 0,
+                   stage: int = 0):
+    t = _Tuning(int(tile), int(unit_bands), int(line_ctas), int(stage), 0.0)
     _check(lib().rqa_set_tuning(ctx.handle, ctypes.byref(t)), "rqa_set_tuning")
 
 

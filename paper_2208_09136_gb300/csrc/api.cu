@@ -56,6 +56,7 @@ struct rqa_ctx {
     int line_tile = 0;      // diagonals per register window of the line pass (0 = default)
     int unit_bands = 0;     // bands per line-pass work unit (0 = planned)
     int line_ctas = 0;      // persistent line-pass CTAs per SM (0 = all that fit)
+    int line_stage = 0;     // line pass: series windows staged by bulk copies (1) or read per lane (0)
     float tuned_ms = 0.f;   // line-pass time of the last rqa_autotune choice
     bool tile_fixed = false;  // the caller chose the tile: rqa_autotune keeps it
     bool loi = false;         // RQA_FLAG_LOI: rates and DET over the whole matrix
@@ -612,6 +613,8 @@ int run_lines(rqa_ctx *c, const Plan &pl, const float *eps, uint64_t *hist, cons
     a.band = c->band;
     a.line_tile = pl.line_tile;
     a.line_ctas = c->line_ctas;
+    a.line_stage = c->line_stage;
+    a.y_len = pl.total;
     a.status = P<int>(c->status);
     unsigned *q = nullptr;
     const int full_grid = persistent_grid(c, (size_t)1 << 30);
@@ -918,7 +921,7 @@ int rqa_det_avg(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t r
         auto put = [&](uint64_t v) { sig.push_back(v); };
         auto ptr = [&](const void *p) { put((uint64_t)(uintptr_t)p); };
         put((uint64_t)pl.S); put((uint64_t)K); put((uint64_t)n_lmin); put((uint64_t)rr_den);
-        put(bracket); put((uint64_t)c->schedule); put((uint64_t)pl.line_tile); put((uint64_t)c->unit_bands); put((uint64_t)c->line_ctas); put(c->timing);
+        put(bracket); put((uint64_t)c->schedule); put((uint64_t)pl.line_tile); put((uint64_t)c->unit_bands); put((uint64_t)c->line_ctas); put((uint64_t)c->line_stage); put(c->timing);
         for (int s = 0; s < pl.S; ++s) put(pl.dom[s]);
         put(c->loi);
         uint32_t mb;
@@ -1188,11 +1191,13 @@ int rqa_set_tuning(rqa_ctx *c, const rqa_tuning *t)
 {
     if (!c || !t) return RQA_ERR_INVALID_ARG;
     if (t->tile != 0 && t->tile != 8 && t->tile != 16 && t->tile != 32) return RQA_ERR_INVALID_ARG;
-    if (t->unit_bands < 0 || t->unit_bands > 64 || t->line_ctas < 0 || t->line_ctas > 8)
+    if (t->unit_bands < 0 || t->unit_bands > 64 || t->line_ctas < 0 || t->line_ctas > 8 ||
+        (t->stage != 0 && t->stage != 1))
         return RQA_ERR_INVALID_ARG;
     c->line_tile = t->tile;
     c->unit_bands = t->unit_bands;
     c->line_ctas = t->line_ctas;
+    c->line_stage = t->stage;
     return RQA_OK;
 }
 
@@ -1202,6 +1207,7 @@ int rqa_get_tuning(rqa_ctx *c, rqa_tuning *t)
     t->tile = c->line_tile ? c->line_tile : LINE_TILE_DEFAULT;
     t->unit_bands = c->unit_bands;
     t->line_ctas = c->line_ctas;
+    t->stage = c->line_stage;
     t->ms = c->tuned_ms;
     return RQA_OK;
 }
@@ -1224,13 +1230,15 @@ int rqa_autotune(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t 
         cells += pc;
     }
     sb.n_series = j;
-    const int saved[3] = {c->line_tile, c->unit_bands, c->line_ctas};
+    const int saved[4] = {c->line_tile, c->unit_bands, c->line_ctas, c->line_stage};
+    c->line_stage = 0;
     c->unit_bands = 0;  // the planned unit size, for the probe's plan
     c->line_ctas = 0;
     Plan probe;
     const int rcp = make_plan(c, &sb, nullptr, 0, K, probe);
     c->unit_bands = saved[1];
     c->line_ctas = saved[2];
+    c->line_stage = saved[3];
     if (rcp) return rcp;
     if (probe.ne_max > LINE_NE_MAX) return RQA_ERR_CAPACITY;
     if (int rc = ensure(c->eps_tmp, (size_t)sb.n_series * K * 4)) return rc;
@@ -1245,6 +1253,7 @@ int rqa_autotune(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t 
         return check_cuda(cudaGetLastError());
     c->unit_bands = 0;
     c->line_ctas = 0;
+    c->line_stage = 0;
     // the line pass over the probe with the context's current knobs, best of two
     auto time_lines = [&](float *best) {
         float t_min = 3.4e38f;
@@ -1303,12 +1312,25 @@ int rqa_autotune(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t 
         }
     }
     c->line_ctas = best_ctas;
+    // 4. series windows staged by bulk copies, where the variant exists
+    int best_stage = 0;
+    if (rc == RQA_OK && lines_stage_ok(probe.mt, c->line_tile)) {
+        c->line_stage = 1;
+        float ms = 0.f;
+        time_lines(&ms);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_stage = 1;
+        }
+    }
+    c->line_stage = best_stage;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != RQA_OK) {
         c->line_tile = saved[0];
         c->unit_bands = saved[1];
         c->line_ctas = saved[2];
+        c->line_stage = saved[3];
         return rc;
     }
     c->tuned_ms = best_ms;

@@ -7,7 +7,6 @@
 
 namespace rqa {
 
-int lines_smem_bytes(int) { return lines_smem_bytes_impl(); }
 
 // Window widths the cell phase supports for an embedding variant: 8, 16 and
 // 32 diagonals for the compile-time embeddings of the diagonal pass, 16
@@ -19,9 +18,15 @@ bool lines_tile_ok(int embed, int tile)
     return special && (tile == 8 || tile == 32);
 }
 
-// The kernel of an embedding variant and register window.
-static LinesKernel lines_kernel(int embed, int tile, bool vert)
+bool lines_stage_ok(int embed, int tile)
 {
+    return lines_kernel_staged(embed, tile) != nullptr;
+}
+
+// The kernel of an embedding variant and register window.
+static LinesKernel lines_kernel(int embed, int tile, bool vert, bool stage)
+{
+    if (stage) return lines_kernel_staged(embed, tile);
     switch (embed) {
     case E_M3T3: return lines_kernel_m3t3(tile, vert);
     case E_M3T1: return lines_kernel_m3t1(tile, vert);
@@ -42,8 +47,11 @@ static cudaError_t launch_lines_v(const CellArgs &a, const LineBufs &lb, int K, 
         K > LINE_KMAX || lb.k0 < 0 || lb.k0 + K > lb.kstride || grid < 1 || a.n_units < 1 ||
         a.n_pos < 1 || a.chunk < 1)
         return cudaErrorInvalidValue;
-    LinesKernel kern = lines_kernel(embed, a.line_tile, VERT);
-    const int smem = lines_smem_bytes(K);
+    // staging where the variant exists; elsewhere the flag is ignored
+    const bool stage = !VERT && a.line_stage && lines_stage_ok(embed, a.line_tile);
+    if (stage && a.y_len < 1) return cudaErrorInvalidValue;
+    LinesKernel kern = lines_kernel(embed, a.line_tile, VERT, stage);
+    const int smem = lines_smem_bytes_impl(stage);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     grid *= WARPS / LWARPS;  // the caller counts CTAs of WARPS warps

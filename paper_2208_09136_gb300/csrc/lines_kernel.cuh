@@ -74,10 +74,54 @@ static_assert(LSH > WSH, "lengths WSH+1..LSH go to the global short histogram");
 constexpr int O_LQ = 0, O_PL = O_LQ + KT * LD * 2, O_PL4 = O_PL + LD * 4, O_EPS = O_PL4 + LD,
               O_TAB = O_EPS + 32, O_HS = O_TAB + TMAX, WARP_WORDS = (O_HS + HROW * 32 + 3) & ~3;
 
+// Staged variant (diagonal pass, register windows): after hs, the series
+// values of one interior row block as the bulk-copy engine brings them in
+//   srow  [SR]  the rows' values y[i0 - 3 .. i0 + 32 + (m-1) tau + 3), 16-byte aligned
+//   scol  [SC]  the columns' values from y[i0 + d_lo - 3 ..], 16-byte aligned
+//   bar   one mbarrier (8 bytes) that counts the two copies' bytes
+constexpr int SR = 44, SC = 72;
+constexpr int O_STG = WARP_WORDS, O_BAR = O_STG + SR + SC, WARP_WORDS_ST = (O_BAR + 2 + 3) & ~3;
+static_assert(O_STG % 4 == 0 && (O_STG + SR) % 4 == 0 && O_BAR % 2 == 0, "copy and barrier alignment");
+constexpr uint32_t STAGE_SPIN = 1u << 20;  // polls of a staged block's barrier before giving up
+
 // CTAs of 2 warps: eight fit per SM (shared memory and registers), sixteen warps
 constexpr int LTHREADS = 64;
 constexpr int LWARPS = LTHREADS / 32;
-inline int lines_smem_bytes_impl() { return LWARPS * WARP_WORDS * 4; }
+inline int lines_smem_bytes_impl(bool stage) { return LWARPS * (stage ? WARP_WORDS_ST : WARP_WORDS) * 4; }
+
+// mbarrier and 1-D bulk copy (global -> this CTA's shared memory) in inline PTX.
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(count) : "memory");
+}
+// the barrier's initialisation made visible to the copy engine (async proxy),
+// and, before a copy overwrites a buffer, the generic-proxy reads of it ordered first
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// one arrival that also announces `bytes` of copies completing on the barrier
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes)
+                 : "memory");
+}
+// dst and src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        :: "r"(dst), "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(bar) : "memory");
+}
+// true once the barrier's phase of the given parity has completed
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
 
 // Recurrence word of threshold k over the 32 rows: bit t = [r_t <= k], i.e.
 // the borrow out of r_t - (k+1) rippled through the bit planes B[0..4] of the
@@ -172,13 +216,19 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane)
     return x;
 }
 
-template <int M, int TAU, int JC, bool VERT>
+// STAGE: the interior row blocks' series values come into shared memory by
+// bulk copies (one per segment, issued by lane 0 for the next row block while
+// the current one computes) instead of per-lane loads through L1.
+template <int M, int TAU, int JC, bool VERT, bool STAGE = false>
 __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, int K)
 {
     static_assert(LD % JC == 0 && JC % 4 == 0, "windows of whole plane-4 groups");
+    static_assert(!STAGE || (TAU > 0 && !VERT && ((32 + (M - 1) * TAU + 6) & ~3) <= SR &&
+                             ((31 + LD + (M - 1) * TAU + 6) & ~3) <= SC),
+                  "staging: register windows of the diagonal pass that fit the buffers");
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *ws = reinterpret_cast<uint32_t *>(smem) + warp * WARP_WORDS;
+    uint32_t *ws = reinterpret_cast<uint32_t *>(smem) + warp * (STAGE ? WARP_WORDS_ST : WARP_WORDS);
     uint32_t *pl = ws + O_PL, *pl4 = ws + O_PL4, *epsb = ws + O_EPS, *tab = ws + O_TAB;
     uint32_t *hs = ws + O_HS + lane;  // this lane's column: [l * 32], threshold k = lane
     uint2 *lqa = reinterpret_cast<uint2 *>(ws + O_LQ);  // [k * LD + j]
@@ -191,6 +241,18 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
     const bool klane = lane < K;
 
     for (int l = 0; l < HROW; ++l) hs[l * 32] = 0;
+
+    // staging state (warp-uniform): the buffers hold at most one row block
+    float *const srow = reinterpret_cast<float *>(ws + O_STG), *const scol = srow + SR;
+    const uint32_t sbar = static_cast<uint32_t>(__cvta_generic_to_shared(ws + O_BAR));
+    bool son = STAGE && (reinterpret_cast<uintptr_t>(a.y) & 15u) == 0;  // copies allowed
+    bool sinf = false;      // a copy issued and not yet waited for
+    uint32_t sph = 0;       // parity of the barrier phase that copy completes
+    int srs = 0, scs = 0;   // offsets of y[i0] in srow and of y[i0 + d_lo] in scol
+    if (STAGE && lane == 0) {
+        mbar_init(sbar, 1);
+        fence_proxy_async_smem();
+    }
     __syncwarp();
     uint64_t lmass = 0;  // lane k: cells on lines of threshold k longer than WSH (this unit)
     uint32_t lmx = 0;    // lane k: the longest of them
@@ -335,6 +397,46 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
             lb.hist ? lb.hist + lb.hist_off[s] + (int64_t)lb.k0 * hrow : nullptr;
         uint64_t *const gshort = lb.hshort + ((int64_t)s * lb.kstride + lb.k0) * LSH;
 
+        // Staging of interior row block i0 of the band at d_lo: the values of
+        // its rows, y[i0 .. i0 + 32 + (m-1) tau), and of its columns,
+        // y[i0 + d_lo .. i0 + d_lo + 31 + LD + (m-1) tau), both widened to
+        // 16-byte boundaries; only when the widened segments stay inside the
+        // batch buffer (else the block reads global memory).  The caller has
+        // finished reading the buffers.
+        auto stage_issue = [&](int i0, int d_lo) -> bool {
+            const int64_t gr = sd.off + i0, gc = gr + d_lo;
+            const int64_t ar = gr & ~(int64_t)3, ac = gc & ~(int64_t)3;
+            const int64_t er = (gr + 32 + (M - 1) * TAU + 3) & ~(int64_t)3;
+            const int64_t ec = (gc + 31 + LD + (M - 1) * TAU + 3) & ~(int64_t)3;
+            if (er > a.y_len || ec > a.y_len) return false;
+            srs = (int)(gr - ar);
+            scs = (int)(gc - ac);
+            __syncwarp();  // every lane's reads of the buffers done
+            if (lane == 0) {
+                const uint32_t br = (uint32_t)(er - ar) * 4u, bc = (uint32_t)(ec - ac) * 4u;
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(sbar, br + bc);
+                bulk_g2s(static_cast<uint32_t>(__cvta_generic_to_shared(srow)), a.y + ar, br, sbar);
+                bulk_g2s(static_cast<uint32_t>(__cvta_generic_to_shared(scol)), a.y + ac, bc, sbar);
+            }
+            sinf = true;
+            return true;
+        };
+        // wait (bounded) for the staged block; on a time-out the block reads
+        // global memory, staging stops and the status records RQA_ERR_TIMEOUT
+        auto stage_wait = [&]() -> bool {
+            bool ok = false;
+            for (uint32_t it = 0; it < STAGE_SPIN && !ok; ++it) ok = mbar_try_wait(sbar, sph);
+            if (__all_sync(FULL, ok)) {
+                sph ^= 1u;
+                sinf = false;
+                return true;
+            }
+            son = false;
+            if (lane == 0) set_status(a.status, 6 /*TIMEOUT*/);
+            return false;
+        };
+
         // lane k: a line of threshold k longer than WSH (rare): its length
         // into the series' short histogram or the caller's full one
         auto emit_rare = [&](uint32_t len) {
@@ -413,17 +515,30 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
                 uint32_t st[KT];
 #pragma unroll
                 for (int k = 0; k < KT; ++k) st[k] = 0;
+                bool staged = false;  // the next interior row block is in the buffers
 
                 // cell phase of the 32 rows i0..i0+31: bit planes of the ranks
                 // of every diagonal into pl / pl4.  INTERIOR: every cell of the
                 // block inside the triangle (no bounds checks).
-                auto cell_phase = [&](int i0, auto interior) {
+                // STAGE: `next` says that row block i0 + 32 is interior too;
+                // its copy is issued once this block's windows are in registers.
+                auto cell_phase = [&](int i0, auto interior, bool next) {
                     constexpr bool INTERIOR = decltype(interior)::value;
                     const int i = i0 + lane;
+                    bool from_smem = false;
+                    if (STAGE && INTERIOR && staged) {
+                        from_smem = stage_wait();
+                        staged = false;
+                    }
 #pragma unroll 1
                     for (int jc = 0; jc < LD; jc += JC) {
                         BandTile<M, TAU, JC> tile;
-                        if (VERT) {
+                        if constexpr (STAGE) {
+                            if (INTERIOR && from_smem) tile.load_smem(srow + srs, scol + scs + jc, lane);
+                            else if (INTERIOR) tile.load_fast(ys, i, d_lo + jc, sd.tau);
+                            else tile.load(ys, sd.n, i, d_lo + jc, rows, sd.tau, sd.m);
+                            if (INTERIOR && next && son && jc + JC == LD) staged = stage_issue(i0 + 32, d_lo);
+                        } else if (VERT) {
                             if (INTERIOR) tile.load_vert_fast(ys, i, c_lo + jc, sd.tau);
                             else tile.load_vert(ys, sd.n, sd.ne, i, c_lo + jc, sd.tau);
                         } else {
@@ -512,13 +627,14 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
                 int i0 = 0;
                 // interior row blocks: every cell of the block inside the matrix
                 const int i_end = VERT ? (c_lo + LD <= sd.ne ? rows - 31 : 0) : rows - (LD - 1) - 31;
+                if (STAGE && son && i_end > 0) staged = stage_issue(0, d_lo);
                 for (; i0 < i_end; i0 += 32) {
-                    cell_phase(i0, std::true_type{});
+                    cell_phase(i0, std::true_type{}, i0 + 32 < i_end);
                     run_phase();
                     if (++nrb == SETTLE) settle();
                 }
                 for (; i0 < rows; i0 += 32) {
-                    cell_phase(i0, std::false_type{});
+                    cell_phase(i0, std::false_type{}, false);
                     run_phase();
                     if (++nrb == SETTLE) settle();
                 }
@@ -547,6 +663,12 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
         cur = -1;
     }
     flush();
+    // a copy left in flight by a time-out: wait for it (bounded) before the
+    // CTA's shared memory is released
+    if (STAGE && sinf) {
+        bool ok = false;
+        for (uint32_t it = 0; it < STAGE_SPIN && !ok; ++it) ok = mbar_try_wait(sbar, sph);
+    }
 }
 
 }  // namespace rqa
@@ -558,4 +680,5 @@ LinesKernel lines_kernel_m3t3(int tile, bool vert);
 LinesKernel lines_kernel_m3t1(int tile, bool vert);
 LinesKernel lines_kernel_m1t1(int tile, bool vert);
 LinesKernel lines_kernel_generic(int m, bool vert);
+LinesKernel lines_kernel_staged(int embed, int tile);  // nullptr where there is none
 }  // namespace rqa

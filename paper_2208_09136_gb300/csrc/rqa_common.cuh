@@ -79,6 +79,15 @@ struct BandTile {
 #pragma unroll
         for (int x = 0; x < D + (M - 1) * TAU; ++x) w[x] = __ldg(ys + i + d_lo + x);
     }
+    // the same window from shared memory: rb holds y[i0..], cb y[i0 + d_lo + jc..]
+    // (row i = i0 + lane)
+    __device__ __forceinline__ void load_smem(const float *rb, const float *cb, int lane)
+    {
+#pragma unroll
+        for (int q = 0; q < M; ++q) a[q] = rb[lane + q * TAU];
+#pragma unroll
+        for (int x = 0; x < D + (M - 1) * TAU; ++x) w[x] = cb[lane + x];
+    }
     // vertical pass: row i, columns c_lo .. c_lo+D-1 (the same window for
     // every lane); zeros outside the series
     __device__ __forceinline__ void load_vert(const float *__restrict__ ys, int n, int ne, int i,

@@ -87,6 +87,8 @@ struct CellArgs {
     int32_t chunk;           // bands per unit
     int32_t line_tile;       // diagonals per register window of the line pass (8, 16 or 32)
     int32_t line_ctas;       // persistent CTAs of the line pass per SM (0: as many as fit)
+    int32_t line_stage;      // line pass: stage the series windows by bulk copies (where supported)
+    int64_t y_len;           // values in the batch buffer y (bulk copies stay below it)
     int64_t n_units;
     unsigned int *queue;   // ticket counter (64-bit aligned), zeroed before launch
     int *status;
@@ -119,6 +121,8 @@ cudaError_t launch_lines(const CellArgs &a, const LineBufs &lb, int K, int grid,
 cudaError_t launch_vlines(const CellArgs &a, const LineBufs &lb, int K, int grid, int embed,
                           cudaStream_t st);
 bool lines_tile_ok(int embed, int tile);
+// The diagonal pass of this embedding and window has a staged variant.
+bool lines_stage_ok(int embed, int tile);
 cudaError_t launch_finalize_det(const LineBufs &lb, const SeriesDev *series, int S, int K,
                                 const int32_t *lmin_dev, int n_lmin, double *det,
                                 double *det_avg, bool loi, cudaStream_t st);
@@ -138,6 +142,5 @@ cudaError_t launch_finalize_hist(const LineBufs &lb, const SeriesDev *series, in
 
 // Largest dynamic shared memory a count round needs for K thresholds.
 int count_smem_bytes(int round, int K);
-int lines_smem_bytes(int K);
 
 }  // namespace rqa

@@ -1,12 +1,13 @@
 """Time the line pass alone on a named workload.
 
-``python -m paper_2208_09136_gb300.linebench WORKLOAD [REPS] [TILE]``
+``python -m paper_2208_09136_gb300.linebench WORKLOAD [REPS] [TILE] [STAGE]``
 
 Builds the workload's batch on cuda:0, selects the thresholds for RR = 1..20 %
 once (``rqa_eps_for_rr``, radix selection), then runs ``rqa_line_hist`` (full
 histograms) REPS times, each timed with CUDA events on the context's stream,
 and prints one line per run.  TILE fixes the cell phase's register window
-(8, 16 or 32; 0 = the default).  Besides the workloads of ``synth``, "mix-m3t3"
+(8, 16 or 32; 0 = the default); STAGE = 1 stages the series windows in
+shared memory by bulk copies (where the variant exists).  Besides the workloads of ``synth``, "mix-m3t3"
 is a 12-series m = tau = 3 set (sine, logistic, Lorenz x SNR -10/0/10/20 dB,
 N = 2e4): the headline workload's line statistics at a size a full profiler
 capture handles.
@@ -39,9 +40,11 @@ def main(argv=None) -> int:
     name = argv[0] if argv else "batched-720"
     reps = int(argv[1]) if len(argv) > 1 else 3
     tile = int(argv[2]) if len(argv) > 2 else 0
+    stage = int(argv[3]) if len(argv) > 3 else 0
     flat, offsets, m, tau = batch_arrays(name)
     stream = torch.cuda.Stream()
     ctx = abi.Context(stream=stream, select=abi.RQA_SELECT_RADIX, tile=tile)
+    abi.rqa_set_tuning(ctx, tile, 0, 0, stage)
     with torch.cuda.stream(stream):
         y = torch.from_numpy(flat).cuda()
     batch = abi.Batch(y, offsets, m, tau)
@@ -63,7 +66,7 @@ def main(argv=None) -> int:
         e1.record(stream)
         stream.synchronize()
         ms = e0.elapsed_time(e1)
-        print(f"{name} tile={abi.rqa_device_info(ctx)['tile']} run {r}: {ms:.2f} ms, "
+        print(f"{name} tile={abi.rqa_device_info(ctx)['tile']} stage={stage} run {r}: {ms:.2f} ms, "
               f"{cells / (ms * 1e-3):.4g} cells/s")
     code = abi.rqa_status(ctx)
     ctx.close()

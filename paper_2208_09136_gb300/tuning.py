@@ -68,10 +68,10 @@ def tuned(ctx: abi.Context, batch: abi.Batch, rr_num, rr_den: int, path: Optiona
     entries = load(path)
     hit = entries.get(key)
     if isinstance(hit, dict) and {"tile", "unit_bands", "line_ctas"} <= set(hit):
-        abi.rqa_set_tuning(ctx, hit["tile"], hit["unit_bands"], hit["line_ctas"])
+        abi.rqa_set_tuning(ctx, hit["tile"], hit["unit_bands"], hit["line_ctas"], hit.get("stage", 0))
         return dict(abi.rqa_get_tuning(ctx), cached=True, key=key)
     got = abi.rqa_autotune(ctx, batch, rr_num, rr_den)
     entries = load(path)  # another process may have written meanwhile
-    entries[key] = {k: got[k] for k in ("tile", "unit_bands", "line_ctas", "ms")}
+    entries[key] = {k: got[k] for k in ("tile", "unit_bands", "line_ctas", "stage", "ms")}
     store(entries, path)
     return dict(got, cached=False, key=key)

@@ -38,7 +38,7 @@ def test_binding_resolves_every_symbol(built):
     L = rqa.lib()
     for name in _declared("rqa.h"):
         assert hasattr(L, name)
-    assert rqa.rqa_abi_version() == 2
+    assert rqa.rqa_abi_version() == 3
 
 
 @pytest.mark.parametrize("p", [1, 3, 4753, 49975003, 4999350021, (1 << 61) + 12345])

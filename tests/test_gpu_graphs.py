@@ -165,6 +165,7 @@ def test_autotune_picks_a_supported_tile_and_stays_exact(rqa_lib):
     run = _Run(rqa, ctx, ys, 3, 3, stream)
     t = rqa.rqa_autotune(ctx, run.batch, RR20, 100)
     assert t["tile"] in (8, 16, 32) and 0 <= t["unit_bands"] <= 64 and t["line_ctas"] in (0, 6)
+    assert t["stage"] in (0, 1)
     assert t["ms"] > 0
     assert rqa.rqa_device_info(ctx)["tile"] == t["tile"]
     assert {k: v for k, v in rqa.rqa_get_tuning(ctx).items() if k != "ms"} == \
@@ -176,8 +177,15 @@ def test_autotune_picks_a_supported_tile_and_stays_exact(rqa_lib):
     _against_oracle(run.call(), ys, 3, 3)
     rqa.rqa_set_tuning(ctx, tile=32, unit_bands=64, line_ctas=8)
     _against_oracle(run.call(), ys, 3, 3)
+    # series windows staged by bulk copies, both windows
+    for tile in (16, 32):
+        rqa.rqa_set_tuning(ctx, tile=tile, stage=1)
+        assert rqa.rqa_get_tuning(ctx)["stage"] == 1
+        _against_oracle(run.call(), ys, 3, 3)
     with pytest.raises(rqa.RqaError):
         rqa.rqa_set_tuning(ctx, tile=12)
+    with pytest.raises(rqa.RqaError):
+        rqa.rqa_set_tuning(ctx, stage=2)
     # a context created with an explicit tile keeps it
     ctx2 = rqa.Context(stream=stream, select=rqa.RQA_SELECT_RADIX, tile=8)
     assert rqa.rqa_autotune(ctx2, run.batch, RR20, 100)["tile"] == 8

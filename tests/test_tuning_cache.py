@@ -17,16 +17,16 @@ def test_batch_key_classes():
 def test_tuned_stores_then_reuses(tmp_path, monkeypatch):
     from paper_2208_09136_gb300 import abi, tuning
     calls = {"autotune": 0, "set": []}
-    state = {"tile": 16, "unit_bands": 0, "line_ctas": 0, "ms": 0.0}
+    state = {"tile": 16, "unit_bands": 0, "line_ctas": 0, "stage": 0, "ms": 0.0}
 
     def fake_autotune(ctx, batch, rr, den):
         calls["autotune"] += 1
-        state.update(tile=32, unit_bands=4, line_ctas=6, ms=1.5)
+        state.update(tile=32, unit_bands=4, line_ctas=6, stage=1, ms=1.5)
         return dict(state)
 
-    def fake_set(ctx, tile=0, unit_bands=0, line_ctas=0):
-        calls["set"].append((tile, unit_bands, line_ctas))
-        state.update(tile=tile, unit_bands=unit_bands, line_ctas=line_ctas)
+    def fake_set(ctx, tile=0, unit_bands=0, line_ctas=0, stage=0):
+        calls["set"].append((tile, unit_bands, line_ctas, stage))
+        state.update(tile=tile, unit_bands=unit_bands, line_ctas=line_ctas, stage=stage)
 
     monkeypatch.setattr(abi, "rqa_autotune", fake_autotune)
     monkeypatch.setattr(abi, "rqa_set_tuning", fake_set)
@@ -42,7 +42,7 @@ def test_tuned_stores_then_reuses(tmp_path, monkeypatch):
     first = tuning.tuned(None, FakeBatch(), list(range(1, 21)), 100, path=path, gpu_name="GB300")
     assert first["cached"] is False and calls["autotune"] == 1
     assert json.load(open(path))[first["key"]]["tile"] == 32
-    state.update(tile=16, unit_bands=0, line_ctas=0)
+    state.update(tile=16, unit_bands=0, line_ctas=0, stage=0)
     second = tuning.tuned(None, FakeBatch(), list(range(1, 21)), 100, path=path, gpu_name="GB300")
     assert second["cached"] is True and calls["autotune"] == 1
-    assert calls["set"] == [(32, 4, 6)]
+    assert calls["set"] == [(32, 4, 6, 1)]
