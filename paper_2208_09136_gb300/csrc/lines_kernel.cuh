@@ -230,15 +230,24 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *ws = reinterpret_cast<uint32_t *>(smem) + warp * (STAGE ? WARP_WORDS_ST : WARP_WORDS);
     uint32_t *pl = ws + O_PL, *pl4 = ws + O_PL4, *epsb = ws + O_EPS, *tab = ws + O_TAB;
-    uint32_t *hs = ws + O_HS + lane;  // this lane's column: [l * 32], threshold k = lane
+    uint32_t *hs = ws + O_HS + lane;  // this lane's column: [l * 32], threshold kk (below)
     uint2 *lqa = reinterpret_cast<uint2 *>(ws + O_LQ);  // [k * LD + j]
     unsigned char *rkm = reinterpret_cast<unsigned char *>(ws + O_LQ);  // rank matrix [j][t]
     uint2 *lq = lqa + lane;                               // slots of this lane's diagonal
-    // lane k: the bits of k + 1 as masks, for its own recurrence words
+    const bool klane = lane < K;
+    // Lines of length >= 4: lane k < K measures those of threshold k; the
+    // 32 - K lanes left over help the top thresholds (the ones with the most
+    // lines), lane L >= K taking threshold L - (32 - K) on the odd diagonals
+    // while that threshold's own lane keeps the even ones.  kk: the threshold
+    // a lane measures (-1: none); its histogram column is its own.
+    const int kpart = lane - (32 - K);  // lane >= K: the threshold it helps (< 0: none)
+    const int kk = klane ? lane : kpart;
+    const uint32_t dsel = klane ? (lane >= 2 * K - 32 ? 0x55555555u : FULL)
+                                : (kpart >= 0 ? 0xAAAAAAAAu : 0u);
+    // the bits of kk + 1 as masks, for rebuilding the recurrence words of threshold kk
     uint32_t kbm[5];
 #pragma unroll
-    for (int b = 0; b < 5; ++b) kbm[b] = (((lane + 1) >> b) & 1) ? FULL : 0u;
-    const bool klane = lane < K;
+    for (int b = 0; b < 5; ++b) kbm[b] = (((kk + 1) >> b) & 1) ? FULL : 0u;
 
     for (int l = 0; l < HROW; ++l) hs[l * 32] = 0;
 
@@ -254,8 +263,8 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
         fence_proxy_async_smem();
     }
     __syncwarp();
-    uint64_t lmass = 0;  // lane k: cells on lines of threshold k longer than WSH (this unit)
-    uint32_t lmx = 0;    // lane k: the longest of them
+    uint64_t lmass = 0;  // cells on lines of threshold kk longer than WSH (this unit, this lane)
+    uint32_t lmx = 0;    // the longest of them
 
     int cur = -1;
     bool bad = false;
@@ -295,14 +304,15 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
         __syncwarp();
     };
 
-    // lane k: column k to the series' short histogram; C_k is the line mass,
-    // sum over l of l * P_k(l) (every recurrent cell lies on exactly one line
-    // of its diagonal), and L_max the longest line
+    // a lane's column to the short histogram of threshold kk (both lanes of a
+    // helped threshold add theirs); C_k is the line mass, sum over l of
+    // l * P_k(l) (every recurrent cell lies on exactly one line of its
+    // diagonal), and L_max the longest line
     auto flush = [&]() {
         if (cur < 0) return;
         settle();
-        if (klane) {
-            const int64_t o = (int64_t)cur * lb.kstride + lb.k0 + lane;
+        if (kk >= 0) {
+            const int64_t o = (int64_t)cur * lb.kstride + lb.k0 + kk;
             uint64_t *gs = lb.hshort + o * LSH;
             uint64_t cnt = lmass;
             uint32_t lm = lmx;
@@ -437,16 +447,16 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
             return false;
         };
 
-        // lane k: a line of threshold k longer than WSH (rare): its length
-        // into the series' short histogram or the caller's full one
+        // a line of threshold kk longer than WSH (rare): its length into the
+        // series' short histogram or the caller's full one
         auto emit_rare = [&](uint32_t len) {
             lmx = max(lmx, len);
             lmass += len;
             if (len <= (uint32_t)LSH)
-                atomicAdd(reinterpret_cast<unsigned long long *>(gshort + (int64_t)lane * LSH + (len - 1)),
+                atomicAdd(reinterpret_cast<unsigned long long *>(gshort + (int64_t)kk * LSH + (len - 1)),
                           1ull);
             else if (hbase)
-                atomicAdd(reinterpret_cast<unsigned long long *>(hbase + (int64_t)lane * hrow + (len - 1)),
+                atomicAdd(reinterpret_cast<unsigned long long *>(hbase + (int64_t)kk * hrow + (len - 1)),
                           1ull);
         };
 
@@ -465,14 +475,17 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
         auto long_lines = [&](uint32_t mask) {
             if (!__any_sync(FULL, mask != 0u)) return;
             __syncwarp();  // every lane's slots written before other lanes read them
-            uint32_t diag = transpose32(mask, lane);  // lane k: diagonals j with lines
+            // lane k: diagonals j with lines of threshold k; then the share of the
+            // lane's own threshold kk (all, the even or the odd diagonals)
+            uint32_t diag = transpose32(mask, lane);
+            diag = __shfl_sync(FULL, diag, kk < 0 ? 0 : kk) & dsel;
             uint32_t x = 0, wq = 0, cq = 0;           // the slot being read
             const uint32_t hcol = static_cast<uint32_t>(__cvta_generic_to_shared(hs));
             while (__any_sync(FULL, (x | diag) != 0u)) {
                 if (x == 0u && diag != 0u) {  // the next diagonal's slot
                     const int j = __ffs(diag) - 1;
                     diag &= diag - 1u;
-                    const uint2 q = lqa[lane * LD + j];
+                    const uint2 q = lqa[kk * LD + j];
                     x = q.x;
                     cq = q.y;
                     const uint4 b4 = *reinterpret_cast<const uint4 *>(pl + j * 4);
