@@ -19,8 +19,8 @@
 //         row t-1 is recurrent and row t is not; copies of the word shifted
 //         down by 1..4 rows (the rows above the block come from the state
 //         carried from the previous block) tell whether that line is at least
-//         2, 3 or 4 long, so lines of length 1, 2 and 3 are counted with three
-//         popcounts per word.  Lines of length >= 4 are measured one by one
+//         2, 3 or 4 long, so lines of length >= 1, 2 and 3 are counted with
+//         three popcounts per word.  Lines of length >= 4 are measured one by one
 //         from the nearest non-recurrent row above their end, or from the
 //         carried run length when the run started in an earlier block.
 //
@@ -29,8 +29,9 @@
 // row block to the next (per lane and threshold) is the top four bits of the
 // previous word and the length of the run open at its last row.
 //
-// Outputs per (series, threshold): P_k(l) (lengths 1..3 as packed register
-// tallies, 4..WSH in the warp's shared histogram, both flushed once per work
+// Outputs per (series, threshold): P_k(l) (lengths 1..3 from packed register
+// tallies, less the lines measured one by one for length 3; 4..WSH in the
+// warp's shared histogram; both flushed once per work
 // unit; WSH+1..LSH in the series' global short histogram; longer lines to the
 // caller's full histogram), L_max, and C_k = sum of l P_k(l), the recurrent
 // cells.
@@ -48,7 +49,7 @@ namespace rqa {
 constexpr int LD = 32;        // diagonals (or columns) per band: one per lane in the run phase
 constexpr int KT = LINE_KMAX; // thresholds per sweep: per-lane carry state and tallies in registers
 constexpr int WSH = 44;       // lines of length 4..WSH counted in the warp's shared histogram
-constexpr int HROW = WSH + 1; // lengths 0..WSH of that histogram (row 0 unused)
+constexpr int HROW = WSH + 1; // rows 0..WSH of that histogram (row 0: lines longer than WSH)
 constexpr int TMAX = 384;     // entries of the rank table
 constexpr uint32_t CMASK = 0x0FFFFFFFu;  // carry state: length of the open run ...
 constexpr uint32_t TOP4 = 0xF0000000u;   // ... and the top four rows of the previous word
@@ -69,8 +70,9 @@ static_assert(LSH > WSH, "lengths WSH+1..LSH go to the global short histogram");
 //                 when the lines of length >= 4 are measured)
 //   epsb  [32]    threshold keys of the current series (padding above every key)
 //   tab   [TMAX]  rank table
-//   hs    [HROW][32] line counts by length, column k for threshold k (a lane
-//         owns a bank): lengths 1..3 from the tallies, 4..WSH one by one
+//   hs    [HROW][32] line counts by length, one column (bank) per lane:
+//         rows 1..3 from the tallies (row 3: every line of length >= 3),
+//         rows 4..WSH one by one, row 0 the lines longer than WSH
 constexpr int O_LQ = 0, O_PL = O_LQ + KT * LD * 2, O_PL4 = O_PL + LD * 4, O_EPS = O_PL4 + LD,
               O_TAB = O_EPS + 32, O_HS = O_TAB + TMAX, WARP_WORDS = (O_HS + HROW * 32 + 3) & ~3;
 
@@ -304,29 +306,52 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
         __syncwarp();
     };
 
-    // a lane's column to the short histogram of threshold kk (both lanes of a
-    // helped threshold add theirs); C_k is the line mass, sum over l of
+    // A lane's column to the short histogram of threshold kk (both lanes of a
+    // helped threshold add theirs).  Row 3 of column k holds every line of
+    // length >= 3; those of length >= 4 are counted again one by one (rows
+    // 4..WSH and row 0, in the columns of threshold k's lane and its helper),
+    // so P_k(3) is row 3 less them.  C_k is the line mass, sum over l of
     // l * P_k(l) (every recurrent cell lies on exactly one line of its
-    // diagonal), and L_max the longest line
+    // diagonal), and L_max the longest line.
     auto flush = [&]() {
         if (cur < 0) return;
         settle();
+        const int64_t o = (int64_t)cur * lb.kstride + lb.k0 + (kk < 0 ? 0 : kk);
+        uint64_t *gs = lb.hshort + o * LSH;
+        uint64_t cnt = lmass;
+        uint32_t lm = lmx;
+        uint32_t longer = hs[0];  // this column's lines of length >= 4
+        hs[0] = 0;
+        auto put = [&](int l, uint32_t v) {
+            if (v) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(gs + (l - 1)), (unsigned long long)v);
+                cnt += (uint64_t)l * v;
+                lm = max(lm, (uint32_t)l);
+            }
+        };
         if (kk >= 0) {
-            const int64_t o = (int64_t)cur * lb.kstride + lb.k0 + kk;
-            uint64_t *gs = lb.hshort + o * LSH;
-            uint64_t cnt = lmass;
-            uint32_t lm = lmx;
 #pragma unroll 1
-            for (int l = 1; l <= WSH; ++l) {  // row l: one bank per lane
+            for (int l = 4; l <= WSH; ++l) {  // row l: one bank per lane
                 const uint32_t v = hs[l * 32];
                 if (v) {
-                    atomicAdd(reinterpret_cast<unsigned long long *>(gs + (l - 1)),
-                              (unsigned long long)v);
                     hs[l * 32] = 0;
-                    cnt += (uint64_t)l * v;
-                    lm = max(lm, (uint32_t)l);
+                    longer += v;
+                    put(l, v);
                 }
             }
+        }
+        // lane k: the lines of length >= 4 its helper counted
+        const uint32_t helped = __shfl_sync(FULL, longer, min(lane + 32 - K, 31));
+        if (klane) {
+            if (lane >= 2 * K - 32) longer += helped;
+            put(1, hs[1 * 32]);
+            put(2, hs[2 * 32]);
+            put(3, hs[3 * 32] - longer);
+            hs[1 * 32] = 0;
+            hs[2 * 32] = 0;
+            hs[3 * 32] = 0;
+        }
+        if (kk >= 0) {
             if (cnt) atomicAdd(reinterpret_cast<unsigned long long *>(lb.count + o),
                                (unsigned long long)cnt);
             if (lm) atomicMax(lb.lmax + o, lm);
@@ -452,6 +477,7 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
         auto emit_rare = [&](uint32_t len) {
             lmx = max(lmx, len);
             lmass += len;
+            hs[0] += 1u;  // row 0 of the lane's column: lines longer than WSH
             if (len <= (uint32_t)LSH)
                 atomicAdd(reinterpret_cast<unsigned long long *>(gshort + (int64_t)kk * LSH + (len - 1)),
                           1ull);
@@ -621,10 +647,11 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
                             const uint32_t e2 = e1 & p2;
                             const uint32_t e3 = e2 & p3;
                             const uint32_t e4 = e3 & p4;
-                            // lines of length >= 4 are counted by length below, not here
-                            tal[k] += __popc(e1) + (__popc(e2) << 10) + (__popc(e3) << 20) -
-                                      __popc(e4) * 0x100401u;
-                            if (e4) {  // measured after the loop (rare for noisy series)
+                            // every line counts towards lengths >= 1, 2, 3; those of
+                            // length >= 4 are measured one by one after the loop
+                            // (rare for noisy series) and taken off length 3 at the flush
+                            tal[k] += __popc(e1) + (__popc(e2) << 10) + (__popc(e3) << 20);
+                            if (e4) {
                                 lq[k * LD] = make_uint2(e4, s0 & CMASK);
                                 lmask |= 1u << k;
                             }
@@ -658,11 +685,10 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
                 for (int k = 0; k < KT; ++k) {
                     if (k < K) {
                         const uint32_t c = st[k] & CMASK;
+                        tal[k] += c == 0 ? 0u : c == 1 ? 1u : c == 2 ? 0x401u : 0x100401u;
                         if (c >= 4) {
                             lq[k * LD] = make_uint2(1u, c);
                             bmask |= 1u << k;
-                        } else {
-                            tal[k] += c == 0 ? 0u : c == 1 ? 1u : c == 2 ? 0x401u : 0x100401u;
                         }
                     }
                 }
