@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
                 const uint32_t zb = ~wq & ((1u << t) - 1u);
                 const uint32_t len = zb ? (uint32_t)(t - 32 + __clz(zb)) : (uint32_t)t + cq;
                 x &= x - 1u;
-                red_shared_addr_if(hcol + min(len, (uint32_t)WSH) * 128u, has && len <= (uint32_t)WSH);
+                red_shared_if_le(hcol + min(len, (uint32_t)WSH) * 128u, has ? len : ~0u, (uint32_t)WSH);
                 if (has && len > (uint32_t)WSH) emit_rare(len);
             }
             __syncwarp();  // slots are rewritten by the next block

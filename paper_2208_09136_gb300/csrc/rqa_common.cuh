@@ -14,13 +14,15 @@ __device__ __forceinline__ void set_status(int *status, int code)
     atomicCAS(status, 0, code);
 }
 
-// Add 1 to the shared word at shared-space address a when pred holds, as
-// one predicated reduction (no branch, so a warp whose lanes disagree does
-// not split; a is not touched when pred is false).
-__device__ __forceinline__ void red_shared_addr_if(uint32_t a, bool pred)
+// Add 1 to the shared word at shared-space address a when x <= y
+// (unsigned), as one compare and one predicated reduction: no branch, so a
+// warp whose lanes disagree does not split, and no predicate turned into an
+// integer and back.  a is not touched when x > y; a caller folds a further
+// condition into x (x = ~0u when it fails, with y < ~0u).
+__device__ __forceinline__ void red_shared_if_le(uint32_t a, uint32_t x, uint32_t y)
 {
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\t@q red.shared.add.u32 [%0], 1;\n\t}"
-                 :: "r"(a), "r"((uint32_t)pred) : "memory");
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.le.u32 q, %1, %2;\n\t@q red.shared.add.u32 [%0], 1;\n\t}"
+                 :: "r"(a), "r"(x), "r"(y) : "memory");
 }
 
 // max(a, b, c) in one instruction (three-input FP32 max of sm_100 and later);

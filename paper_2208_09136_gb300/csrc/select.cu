@@ -52,9 +52,9 @@ int count_smem_bytes(int round, int K)
     }
 }
 
-__device__ __forceinline__ void red_shared_if(uint32_t *p, bool pred)
+__device__ __forceinline__ uint32_t smem_addr(const uint32_t *p)
 {
-    red_shared_addr_if(static_cast<uint32_t>(__cvta_generic_to_shared(p)), pred);
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
 // One persistent launch over the work items; each CTA histograms the keys of
@@ -190,17 +190,18 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
                         // keys under klo wrap to rel >= 2^31 (keys are < 2^31)
                         const uint32_t rel = key - klo;
                         below += valid ? rel >> 31 : 0u;
-                        red_shared_addr_if(hsub + ((rel >> 10) << 2), valid && rel <= kspan);
+                        // kspan < 2^31 (a range of finite keys), so ~0u never counts
+                        red_shared_if_le(hsub + ((rel >> 10) << 2), valid ? rel : ~0u, kspan);
                     } else if (ROUND == R_COARSE_SUB) {
                         below += (valid && key < klo) ? 1u : 0u;
                         const int g = t1[c];
                         const int bin = g < 0 ? c : NCOARSE + g * NFINE + fine;
-                        red_shared_if(&h[bin], valid && key - klo <= kspan);
+                        red_shared_if_le(smem_addr(&h[bin]), valid ? key - klo : ~0u, kspan);
                     } else if (ROUND == R_MID) {
                         // groups outside this launch's window [g0, g0 + gn) wait for another
                         const uint32_t gw = (uint32_t)((int)t1[c] - a.g0);
-                        red_shared_if(&h[min(gw, (uint32_t)(nbins_max / NFINE - 1)) * NFINE + fine],
-                                      valid && gw < (uint32_t)a.gn);
+                        red_shared_if_le(smem_addr(&h[min(gw, (uint32_t)(nbins_max / NFINE - 1)) * NFINE + fine]),
+                                         valid ? gw : ~0u, (uint32_t)a.gn - 1u);
                     } else if (FAST) {
                         // one probe: the slot holds the only target prefix
                         // that can map there.  Empty slots hold group 0 with
