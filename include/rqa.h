@@ -39,7 +39,8 @@
  *     slower line pass).
  *   - The line pass (rqa_det_avg, rqa_line_hist, rqa_vline_hist) counts
  *     series with Ne < 2^26 (6.7e7 vectors, 2.2e15 cells); longer ones are
- *     RQA_ERR_CAPACITY.
+ *     RQA_ERR_CAPACITY.  Every call takes series with Ne <= 3 * 2^30 / 32
+ *     (1.0e8 vectors, 5e15 cells), else RQA_ERR_CAPACITY.
  *   - A series must have Ne >= 2 (P >= 1), otherwise RQA_ERR_TOO_SHORT.
  */
 #ifndef RQA_H

@@ -201,6 +201,7 @@ int validate_batch(const rqa_batch *b)
         if (n > (int64_t)0x7fffffff - 64) return RQA_ERR_CAPACITY;
         const int64_t ne = n - (int64_t)(b->m[s] - 1) * b->tau[s];
         if (ne < 2) return RQA_ERR_TOO_SHORT;
+        if (ne > COUNT_NE_MAX) return RQA_ERR_CAPACITY;
     }
     return RQA_OK;
 }
@@ -290,7 +291,7 @@ int make_plan(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_
     tgt = std::min(tgt, cap);
     std::vector<Item> items;
     std::vector<uint64_t> costs;
-    for (int s = 0; s < S; ++s) build_items(pl.sd[s], s, c->band, tgt, 4 * WARPS, items, &costs);
+    for (int s = 0; s < S; ++s) build_items(pl.sd[s], s, c->band, tgt, ITEM_MIN_BANDS, items, &costs);
     std::vector<size_t> idx(items.size());
     for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
     std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) { return costs[x] > costs[y]; });
@@ -299,7 +300,7 @@ int make_plan(rqa_ctx *c, const rqa_batch *b, const int32_t *rr_num, int32_t rr_
     pl.ser_begin.assign(S + 1, 0);
     for (int s = 0; s < S; ++s) {
         uint64_t t = std::min(std::max<uint64_t>(pl.sd[s].P / (ctas * 3), 1), cap);
-        build_items(pl.sd[s], s, c->band, t, 4 * WARPS, pl.items_ser, nullptr);
+        build_items(pl.sd[s], s, c->band, t, ITEM_MIN_BANDS, pl.items_ser, nullptr);
         pl.ser_begin[s + 1] = (int)pl.items_ser.size();
     }
     // warp work units (line pass): runs of `chunk` bands of LINE_BAND

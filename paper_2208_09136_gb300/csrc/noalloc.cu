@@ -182,8 +182,9 @@ extern "C" int rqa_eps_for_rr_noalloc(const rqa_batch *b, const int32_t *rr_num,
         d.P = (uint64_t)ne * (uint64_t)(ne - 1) / 2;
         d.nbands = (int32_t)((ne - 1 + BAND - 1) / BAND);
         if (rqa_target_counts(d.P, rr_num, rr_den, K, pl.T[s]) != RQA_OK) return RQA_ERR_INVALID_ARG;
-        // at least four bands per warp, at most NA_MAX_ITEMS_PER_SERIES items
-        int chunk = 4 * WARPS;
+        // at least ITEM_MIN_BANDS bands (1024 diagonals) per item, at most
+        // NA_MAX_ITEMS_PER_SERIES items
+        int chunk = ITEM_MIN_BANDS;
         while ((d.nbands + chunk - 1) / chunk > NA_MAX_ITEMS_PER_SERIES) chunk *= 2;
         // the largest item is the first (the longest diagonals 1..chunk*BAND);
         // every Ne up to RQA_NOALLOC_NE_MAX passes, this guards the invariant

@@ -22,9 +22,13 @@ constexpr int NSUB_MAX = 24;       // bracket-subdivided coarse buckets per seri
 constexpr int LSH = 64;            // line lengths 1..LSH counted in shared memory
 constexpr int LMIN_MAX = 8;        // entries of an lmin list
 constexpr int THREADS = 256;       // threads per CTA of the cell kernels
-constexpr int BAND = 16;           // diagonals per warp band of the counting rounds
+constexpr int BAND = 32;           // diagonals per warp band of the counting rounds
+constexpr int ITEM_MIN_BANDS = 4 * 16 * 16 / BAND;  // bands of a work item (1024 diagonals) at least
 constexpr int LINE_TILE_DEFAULT = 16;  // diagonals per register window of the line pass's cell phase
 constexpr int LINE_NE_MAX = (1 << 26) - 1;  // vectors per series the line pass counts exactly
+// vectors per series the counting rounds take: a work item holds under 2^30
+// cells plus one band (BAND x Ne), so its 32-bit shared bins cannot overflow
+constexpr int64_t COUNT_NE_MAX = ((int64_t)3 << 30) / BAND;
 constexpr int WARPS = THREADS / 32;
 
 // Counting rounds of the selection.
