@@ -25,6 +25,14 @@ __device__ __forceinline__ void red_shared_if_le(uint32_t a, uint32_t x, uint32_
                  :: "r"(a), "r"(x), "r"(y) : "memory");
 }
 
+// Add 1 to the shared word at shared-space address a: one reduction, no
+// predicate.  A cell that counts nowhere adds to a per-lane scratch word
+// instead, so no branch region is needed around the reduction.
+__device__ __forceinline__ void red_shared(uint32_t a)
+{
+    asm volatile("red.shared.add.u32 [%0], 1;" :: "r"(a) : "memory");
+}
+
 // max(a, b, c) in one instruction (three-input FP32 max of sm_100 and later);
 // exact, like two two-input maxima.
 __device__ __forceinline__ float fmax3(float a, float b, float c)

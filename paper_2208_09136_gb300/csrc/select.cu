@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
     __shared__ int next_band;
     __shared__ uint32_t key_lo, key_hi;
     __shared__ unsigned long long below_sh;
+    __shared__ uint32_t sink[32];  // lane x's reductions of cells that count nowhere (never read)
     const int nbins_max = (ROUND == R_COARSE) ? NCOARSE
                         : (ROUND == R_COARSE_SUB) ? NCOARSE + NSUB_MAX * NFINE
                         : (ROUND == R_MID) ? (K < MID_GROUPS ? K : MID_GROUPS) * NFINE : 0;
@@ -143,6 +144,7 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
         const bool dense = ROUND == R_COARSE_SUB && ((kspan >> COARSE_SHIFT) + 1u) * NFINE + NCOARSE ==
                                                         (uint32_t)nb_used;
         const uint32_t hsub = static_cast<uint32_t>(__cvta_generic_to_shared(h + NCOARSE));
+        const uint32_t sink_a = smem_addr(&sink[lane]);
         // the item's bands; FAST: dense bracket round, or final round with the
         // hashed prefix table
         auto item_bands = [&](auto fast) {
@@ -172,10 +174,15 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
                 }
             };
             // the BAND cells of a lane in one row block; valid = inside the
-            // triangle.  The filtered rounds are branch-free: the bin is
-            // computed for every cell (keys of finite or NaN distances have
-            // bit 31 clear, so key >> 20 indexes the 2048-entry table) and a
-            // predicated reduction counts the cells that fall in one.
+            // triangle.  The filtered rounds compute the bin of every cell
+            // (keys of finite or NaN distances have bit 31 clear, so key >> 20
+            // indexes the 2048-entry table).  The bracket round, where many
+            // cells fall in the range, adds one for every cell with an
+            // unconditional reduction (into the lane's sink word for a cell
+            // outside the range); a conditional one would make the compiler
+            // wrap each cell in a branch region.  The middle round, where few
+            // cells count, uses a predicated reduction, and the final round
+            // branches around its rare global atomics.
             auto row_block = [&](const BandTile<M, TAU, BAND> &tile, int i, bool interior) {
 #pragma unroll
                 for (int j = 0; j < BAND; ++j) {
@@ -190,13 +197,12 @@ __global__ void __launch_bounds__(count_threads(ROUND)) k_count(CellArgs a, SelB
                         // keys under klo wrap to rel >= 2^31 (keys are < 2^31)
                         const uint32_t rel = key - klo;
                         below += valid ? rel >> 31 : 0u;
-                        // kspan < 2^31 (a range of finite keys), so ~0u never counts
-                        red_shared_if_le(hsub + ((rel >> 10) << 2), valid ? rel : ~0u, kspan);
+                        red_shared(valid && rel <= kspan ? hsub + ((rel >> 10) << 2) : sink_a);
                     } else if (ROUND == R_COARSE_SUB) {
                         below += (valid && key < klo) ? 1u : 0u;
                         const int g = t1[c];
                         const int bin = g < 0 ? c : NCOARSE + g * NFINE + fine;
-                        red_shared_if_le(smem_addr(&h[bin]), valid ? key - klo : ~0u, kspan);
+                        red_shared(valid && key - klo <= kspan ? smem_addr(&h[bin]) : sink_a);
                     } else if (ROUND == R_MID) {
                         // groups outside this launch's window [g0, g0 + gn) wait for another
                         const uint32_t gw = (uint32_t)((int)t1[c] - a.g0);
