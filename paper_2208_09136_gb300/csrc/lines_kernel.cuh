@@ -11,9 +11,11 @@
 //         thresholds, or a 5-step search over them) and stores r as byte
 //         [j][t] of a 32 x 32 rank matrix in shared memory.
 //  runs   lane j holds diagonal j.  It reads row j of the matrix (the ranks of
-//         its 32 cells, two 16-byte loads) and gathers their five bit planes
-//         with masks and multiplies (bit p of four bytes lands in four
-//         adjacent bits of a product); then, for every
+//         its 32 cells, two 16-byte loads) and gathers their five bit planes:
+//         two words of four ranks are interleaved bit by bit, so one mask and
+//         one multiply bring bit p of eight ranks into the top byte of a
+//         product, and byte permutes put four such bytes together (the rows
+//         are stored in the byte order this produces); then, for every
 //         threshold k, rebuilds the 32-row recurrence word {t : r_t <= k} (the
 //         borrow out of r - (k+1), two LOP3s).  A line ends at row t-1 where
 //         row t-1 is recurrent and row t is not; copies of the word shifted
@@ -59,8 +61,9 @@ static_assert(LSH > WSH, "lengths WSH+1..LSH go to the global short histogram");
 
 // Per-warp shared memory, in 32-bit words:
 //   lq    [KT][LD] 8 bytes each: when the word of threshold k of diagonal j
-//         ends lines of length >= 4, their end mask and the run open above
-//         the word; they are measured after the threshold loop (the word
+//         ends lines of length >= 4, their end mask and the run state carried
+//         into the word (the run open above it in the low 28 bits); they are
+//         measured after the threshold loop (the word
 //         itself is rebuilt there from the row block's planes).  The same
 //         space first holds the row block's rank matrix, [LD][32] bytes (row
 //         j: the ranks of diagonal j's 32 cells), read before any slot is
@@ -237,6 +240,10 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
     unsigned char *rkm = reinterpret_cast<unsigned char *>(ws + O_LQ);  // rank matrix [j][t]
     uint2 *lq = lqa + lane;                               // slots of this lane's diagonal
     const bool klane = lane < K;
+    // byte of row `lane` in a row of the rank matrix: rows 8h + 2u and 8h + 2u + 1
+    // sit four bytes apart (bytes 8h + u and 8h + u + 4), the order the plane
+    // gather of the run phase reads them in
+    const int rcol = (lane & ~7) | ((lane & 7) >> 1) | ((lane & 1) << 2);
     // Lines of length >= 4: lane k < K measures those of threshold k; the
     // 32 - K lanes left over help the top thresholds (the ones with the most
     // lines), lane L >= K taking threshold L - (32 - K) on the odd diagonals
@@ -513,7 +520,7 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
                     diag &= diag - 1u;
                     const uint2 q = lqa[kk * LD + j];
                     x = q.x;
-                    cq = q.y;
+                    cq = q.y & CMASK;
                     const uint4 b4 = *reinterpret_cast<const uint4 *>(pl + j * 4);
                     wq = rank_le_word_lane(b4.x, b4.y, b4.z, b4.w, pl4[j], kbm);
                 }
@@ -601,7 +608,7 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
                                 const uint32_t rk = rank_of(key);
                                 r = valid ? rk : 31u;
                             }
-                            rkm[(jc + j) * 32 + lane] = (unsigned char)r;
+                            rkm[(jc + j) * 32 + rcol] = (unsigned char)r;
                         }
                     }
                 };
@@ -612,18 +619,34 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
                     const uint4 ra = *reinterpret_cast<const uint4 *>(rkm + lane * 32);
                     const uint4 rb = *reinterpret_cast<const uint4 *>(rkm + lane * 32 + 16);
                     const uint32_t R[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
-                    // bit p of the four ranks of word q (rows 4q..4q+3, one per
-                    // byte): masked, then multiplied so they land in bits 28..31
+                    // Words 2h and 2h + 1 hold rows 8h .. 8h + 7 (byte u of word
+                    // 2h: row 8h + 2u, of word 2h + 1: row 8h + 2u + 1).  X[h]
+                    // interleaves their even bits (bit p of byte u of word 2h
+                    // at p + 8u, of word 2h + 1 at p + 1 + 8u), Xo[h] their odd
+                    // bits one place lower.  For plane p the two bits of each
+                    // byte pair are masked and one multiply by
+                    // 2^24 + 2^18 + 2^12 + 2^6 (shifted down by the pair's bit
+                    // position) moves the eight of them, rows in order, into
+                    // bits 24..31 with no two partial products meeting (so no
+                    // carry reaches the top byte); three byte permutes join the
+                    // four top bytes into the plane.
+                    uint32_t X[4], Xo[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        X[h] = (R[2 * h] & 0x55555555u) | ((R[2 * h + 1] << 1) & 0xAAAAAAAAu);
+                        Xo[h] = ((R[2 * h] >> 1) & 0x55555555u) | (R[2 * h + 1] & 0xAAAAAAAAu);
+                    }
                     uint32_t B[5];
 #pragma unroll
                     for (int p = 0; p < 5; ++p) {
-                        uint32_t b = 0;
+                        const int sh = p & ~1;
+                        uint32_t v[4];
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const uint32_t v = (R[q] & (0x01010101u << p)) * (0x10204080u >> p);
-                            b |= q < 7 ? (v >> (28 - 4 * q)) & (0xFu << (4 * q)) : v & 0xF0000000u;
-                        }
-                        B[p] = b;
+                        for (int h = 0; h < 4; ++h)
+                            v[h] = ((p & 1 ? Xo[h] : X[h]) & (0x03030303u << sh)) * (0x01041040u >> sh);
+                        const uint32_t lo = __byte_perm(v[0], v[1], 0x0073);
+                        const uint32_t hi = __byte_perm(v[2], v[3], 0x7300);
+                        B[p] = __byte_perm(lo, hi, 0x7610);
                     }
                     // this diagonal's planes, for rebuilding words of long lines
                     *reinterpret_cast<uint4 *>(pl + lane * 4) = make_uint4(B[0], B[1], B[2], B[3]);
@@ -651,13 +674,17 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
                             // length >= 4 are measured one by one after the loop
                             // (rare for noisy series) and taken off length 3 at the flush
                             tal[k] += __popc(e1) + (__popc(e2) << 10) + (__popc(e3) << 20);
-                            if (e4) {
-                                lq[k * LD] = make_uint2(e4, s0 & CMASK);
+                            if (e4) {  // the reader takes the run length from the state's low bits
+                                lq[k * LD] = make_uint2(e4, s0);
                                 lmask |= 1u << k;
                             }
-                            // the new state: top rows of this word and the run open at its last row
-                            const uint32_t open = (w == FULL) ? (s0 & CMASK) + 32u : (uint32_t)__clz(~w);
-                            st[k] = (w & TOP4) | open;
+                            // the new state: top rows of this word and the run open at
+                            // its last row.  c = 32 only for an all-ones word, whose run
+                            // continues the one open above: c + s0 has the old length
+                            // + 32 in its low bits (the sum stays under 2^28), and its
+                            // top bits are overwritten by the word's, all ones.
+                            const uint32_t c = __clz(~w);
+                            st[k] = (w & TOP4) | (s0 * (c >> 5) + c);
                         }
                     }
                     long_lines(lmask);
