@@ -59,6 +59,8 @@ def parse():
                     help="skip the batched radix-selection comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the per-call latency of a one-series batch")
     ap.add_argument("--cpu-cells", type=float, default=1.2e8,
                     help="cells of the oracle's bounded sample")
     ap.add_argument("--tile", type=int, default=0,
@@ -443,6 +445,58 @@ def main():
                "d2h_bytes_per_step": int((h_avg.numel() + h_det.numel()) * 8 + h_eps.numel() * 4),
                "ms_per_step": ems, "note": "series H2D, DET/avg DET/eps D2H; P(l) stays on device"}
 
+    # latency of one call on a one-series batch (N = 100 logistic map, m = tau = 1),
+    # where the step is bound by launches, not by cells: median of single calls,
+    # with the inputs resident and end to end (series H2D, DET averages D2H)
+    small = None
+    if rank == 0 and not args.no_small:
+        from synth import workload as make_workload
+        sflat, soff, sm_, stau = make_workload("logistic-n100").pack()
+        sK = len(RR)
+        with torch.cuda.stream(stream):
+            sy = torch.from_numpy(sflat).to(f"cuda:{dev}")
+            sb = rqa.Batch(sy, soff, sm_, stau)
+            shoff = sb.hist_offsets(sK)
+            s_det = torch.empty((1, sK, len(LMIN)), dtype=torch.float64, device=dev)
+            s_avg = torch.empty((1, len(LMIN)), dtype=torch.float64, device=dev)
+            s_eps = torch.empty((1, sK), dtype=torch.float32, device=dev)
+            s_hist = torch.empty(int(shoff[-1]), dtype=torch.uint64, device=dev)
+        h_sy = torch.from_numpy(sflat).pin_memory()
+        h_savg = torch.empty((1, len(LMIN)), dtype=torch.float64).pin_memory()
+        sctx = rqa.Context(device=dev, stream=stream, schedule=rqa.RQA_SCHED_BATCHED,
+                           select=rqa.RQA_SELECT_RADIX)
+
+        def small_call(e2e_copies):
+            if e2e_copies:
+                with torch.cuda.stream(stream):
+                    sy.copy_(h_sy, non_blocking=True)
+            rqa.rqa_det_avg(sctx, sb, RR, 100, None, sK, LMIN, s_det, s_avg, s_eps, s_hist, shoff,
+                            None, None, None)
+            if e2e_copies:
+                with torch.cuda.stream(stream):
+                    h_savg.copy_(s_avg, non_blocking=True)
+
+        res = {}
+        for label, copies in (("resident", False), ("e2e", True)):
+            for _ in range(20):
+                small_call(copies)
+            stream.synchronize()
+            t = []
+            for _ in range(100):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                small_call(copies)
+                e1.record(stream)
+                stream.synchronize()
+                t.append(e0.elapsed_time(e1))
+            res[label] = statistics.median(t)
+        if rqa.rqa_status(sctx):
+            raise SystemExit("device error in the one-series calls")
+        sctx.close()
+        small = {"workload": "logistic-n100: 1 series, N = 100, m = tau = 1, K = 20, radix select",
+                 "ms_per_call": res["resident"], "e2e_ms_per_call": res["e2e"],
+                 "calls": 100, "stat": "median of single calls (CUDA events on the call's stream)"}
+
     # roofline of the dominant kernel (line pass): issue-limited integer/FP32 ALU
     peaks = measured_peaks()
     sm = rqa.rqa_device_info(ctx)["sm_count"]
@@ -501,6 +555,7 @@ def main():
             "e2e": e2e,
             "plain": plain,
             "radix": radix,
+            "small_batch": small,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

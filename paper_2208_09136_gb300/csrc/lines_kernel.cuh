@@ -524,11 +524,17 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
                     const uint4 b4 = *reinterpret_cast<const uint4 *>(pl + j * 4);
                     wq = rank_le_word_lane(b4.x, b4.y, b4.z, b4.w, pl4[j], kbm);
                 }
+                // the lowest end bit t of the slot (lowb = 2^t; 0 when the lane
+                // has no line left); the line ends at row t - 1 and starts below
+                // the nearest non-recurrent row above it, or continues the run
+                // open above the word when rows 0 .. t - 1 are all recurrent
+                // (then clz(zb) = 32): len = t - 32 + clz(zb) + [zb == 0] * cq
                 const bool has = x != 0u;
-                const int t = (__ffs(x) - 1) & 31;
-                const uint32_t zb = ~wq & ((1u << t) - 1u);
-                const uint32_t len = zb ? (uint32_t)(t - 32 + __clz(zb)) : (uint32_t)t + cq;
-                x &= x - 1u;
+                const uint32_t lowb = x & (0u - x);
+                x ^= lowb;
+                const uint32_t zb = ~wq & (lowb - 1u);
+                const uint32_t cz = __clz(zb);
+                const uint32_t len = cz - (uint32_t)__clz(lowb) - 1u + (cz >> 5) * cq;
                 red_shared_if_le(hcol + min(len, (uint32_t)WSH) * 128u, has ? len : ~0u, (uint32_t)WSH);
                 if (has && len > (uint32_t)WSH) emit_rare(len);
             }
