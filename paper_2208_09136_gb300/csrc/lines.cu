@@ -23,14 +23,16 @@ bool lines_stage_ok(int embed, int tile)
     return lines_kernel_staged(embed, tile) != nullptr;
 }
 
-// The kernel of an embedding variant and register window.
-static LinesKernel lines_kernel(int embed, int tile, bool vert, bool stage)
+// The kernel of an embedding variant and register window (full: a sweep of
+// LINE_KMAX thresholds, which the special embeddings' diagonal pass has its
+// own variant for).
+static LinesKernel lines_kernel(int embed, int tile, bool vert, bool stage, bool full)
 {
     if (stage) return lines_kernel_staged(embed, tile);
     switch (embed) {
-    case E_M3T3: return lines_kernel_m3t3(tile, vert);
-    case E_M3T1: return lines_kernel_m3t1(tile, vert);
-    case E_M1T1: return lines_kernel_m1t1(tile, vert);
+    case E_M3T3: return lines_kernel_m3t3(tile, vert, full);
+    case E_M3T1: return lines_kernel_m3t1(tile, vert, full);
+    case E_M1T1: return lines_kernel_m1t1(tile, vert, full);
     case E_M1: case E_M2: case E_M3: case E_M4: return lines_kernel_generic(embed, vert);
     default: return lines_kernel_generic(0, vert);
     }
@@ -50,7 +52,7 @@ static cudaError_t launch_lines_v(const CellArgs &a, const LineBufs &lb, int K, 
     // staging where the variant exists; elsewhere the flag is ignored
     const bool stage = !VERT && a.line_stage && lines_stage_ok(embed, a.line_tile);
     if (stage && a.y_len < 1) return cudaErrorInvalidValue;
-    LinesKernel kern = lines_kernel(embed, a.line_tile, VERT, stage);
+    LinesKernel kern = lines_kernel(embed, a.line_tile, VERT, stage, K == LINE_KMAX);
     const int smem = lines_smem_bytes_impl(stage);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;

@@ -224,9 +224,12 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane)
 // STAGE: the interior row blocks' series values come into shared memory by
 // bulk copies (one per segment, issued by lane 0 for the next row block while
 // the current one computes) instead of per-lane loads through L1.
-template <int M, int TAU, int JC, bool VERT, bool STAGE = false>
-__global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, int K)
+// FK: a full sweep, K = KT thresholds known at compile time (the per-threshold
+// code then runs without a test of k against K); the argument is ignored.
+template <int M, int TAU, int JC, bool VERT, bool STAGE = false, bool FK = false>
+__global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, int K_arg)
 {
+    const int K = FK ? KT : K_arg;
     static_assert(LD % JC == 0 && JC % 4 == 0, "windows of whole plane-4 groups");
     static_assert(!STAGE || (TAU > 0 && !VERT && ((32 + (M - 1) * TAU + 6) & ~3) <= SR &&
                              ((31 + LD + (M - 1) * TAU + 6) & ~3) <= SC),
@@ -748,9 +751,10 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
 namespace rqa {
 using LinesKernel = void (*)(CellArgs, LineBufs, int);
 // Instantiations, one group per translation unit (they compile in parallel).
-LinesKernel lines_kernel_m3t3(int tile, bool vert);
-LinesKernel lines_kernel_m3t1(int tile, bool vert);
-LinesKernel lines_kernel_m1t1(int tile, bool vert);
+// full: the diagonal pass's variant for a sweep of exactly LINE_KMAX thresholds
+LinesKernel lines_kernel_m3t3(int tile, bool vert, bool full);
+LinesKernel lines_kernel_m3t1(int tile, bool vert, bool full);
+LinesKernel lines_kernel_m1t1(int tile, bool vert, bool full);
 LinesKernel lines_kernel_generic(int m, bool vert);
 LinesKernel lines_kernel_staged(int embed, int tile);  // nullptr where there is none
 }  // namespace rqa
