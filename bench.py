@@ -382,6 +382,9 @@ def main():
     radix = None
     if not args.no_radix and form != "plain" and have_model:
         rctx = make_ctx(rqa.RQA_SCHED_BATCHED)  # radix select
+        # the same line-pass knobs as the timed context, so the two legs differ in the
+        # selection alone
+        rqa.rqa_set_tuning(rctx, tuned["tile"], tuned["unit_bands"], tuned["line_ctas"], tuned["stage"])
         rqa.rqa_set_timing(rctx, True)
         step(rctx)
         stream.synchronize()
@@ -402,7 +405,7 @@ def main():
         if rqa.rqa_status(rctx):
             raise SystemExit("device error in the radix form")
         rms = max_over_ranks(rms, dist, dev)
-        radix = {"form": "batched, full radix selection (no network)",
+        radix = {"form": "batched, full radix selection (no network), the timed context's line-pass knobs",
                  "value": world * total_cells / (rms * 1e-3), "series_per_s": world * S / (rms * 1e-3),
                  "ms_per_step": rms, "steps": n_rad,
                  "phase_ms": {n: round(float(v), 4) for n, v in
