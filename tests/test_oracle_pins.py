@@ -5,7 +5,8 @@ Each pin is chosen so that a plausible slip in the oracle (an off-by-one in
 the target count, a strict/inclusive mix-up, a dropped delay coordinate, a
 transposed diagonal, a lost line at a diagonal's end) fails at least one test:
 
-* a hand-worked 4-point example (tests/golden/hand_example_4pt.json);
+* a hand-worked 4-point example (tests/golden/hand_example_4pt.json) and its line
+  measures, vertical lines and line-of-identity reading (hand_example_4pt_measures.json);
 * brute force over the FULL N x N matrix with ordered pairs (a different
   formulation of Eq. 1-4: every count is exactly twice the upper-triangle one);
 * closed forms: constant series, integer ramp, sawtooth;
@@ -42,6 +43,52 @@ def test_hand_example_matches_worked_values():
     assert r["lmax"].tolist() == g["lmax"]
     assert r["det"][:, 0].tolist() == g["det_lmin2"]
     assert float(r["det_avg"][0]) == g["det_avg_lmin2"]
+
+
+def _eq_or_nan(got, want, rtol=0.0):
+    """want None means undefined (NaN); otherwise equal within rtol."""
+    got = np.asarray(got, dtype=np.float64).ravel()
+    flat = [np.nan if w is None else w for w in np.asarray(want, dtype=object).ravel()]
+    want = np.asarray(flat, dtype=np.float64)
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    ok = ~np.isnan(want)
+    assert np.allclose(got[ok], want[ok], rtol=rtol, atol=0.0), (got, want)
+
+
+def test_hand_example_measures_vertical_lines_and_identity_line():
+    """L, ENTR, vertical lines, LAM and TT, and the line-of-identity reading
+    of Eq. 3 and Eq. 4, against values worked by hand for the 4-point series
+    (tests/golden/hand_example_4pt_measures.json)."""
+    g = json.load(open(os.path.join(GOLDEN, "hand_example_4pt_measures.json")))
+    y = np.array(g["y"], dtype=np.float32)
+    m, tau = g["m"], g["tau"]
+    eps = np.array(g["eps"], dtype=np.float32)
+    lines = O.line_hist(y, m, tau, eps)
+    lm = O.line_measures(lines["hist"], g["lmin"])
+    _eq_or_nan(lm["L"], g["L"])
+    _eq_or_nan(lm["entr"], g["entr"], rtol=1e-15)
+    v = O.vline_hist(y, m, tau, eps)
+    assert v["vhist"].tolist() == g["vhist"]
+    assert v["vmax"].tolist() == g["vmax"]
+    lt = O.lam_tt(v["vhist"], lines["count"], g["vmin"], 4)
+    _eq_or_nan(lt["lam"], g["lam"])
+    _eq_or_nan(lt["tt"], g["tt"])
+
+    h = g["loi"]
+    sel = O.eps_for_rr(y, m, tau, h["rr_num"], h["rr_den"], loi=True)
+    assert sel["T"].tolist() == h["T"]
+    assert sel["eps"].tolist() == h["eps"]
+    assert sel["count_le"].tolist() == h["count_le"]
+    ll = O.line_hist(y, m, tau, sel["eps"])
+    _eq_or_nan(O.det_from_hist(ll["hist"], ll["count"], [2], loi=True)[:, 0], h["det_lmin2"], rtol=1e-15)
+    lml = O.line_measures(ll["hist"], [2], loi=True)
+    _eq_or_nan(lml["L"][:, 0], h["L_lmin2"], rtol=1e-15)
+    _eq_or_nan(lml["entr"][:, 0], h["entr_lmin2"], rtol=1e-14)
+    vl = O.vline_hist(y, m, tau, sel["eps"], loi=True)
+    assert vl["vhist"].tolist() == h["vhist"]
+    ltl = O.lam_tt(vl["vhist"], ll["count"], [2], 4, loi=True)
+    _eq_or_nan(ltl["lam"][:, 0], h["lam_vmin2"], rtol=1e-15)
+    _eq_or_nan(ltl["tt"][:, 0], h["tt_vmin2"], rtol=1e-15)
 
 
 # ------------------------------------------------------------ target counts
