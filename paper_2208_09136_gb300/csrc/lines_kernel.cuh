@@ -8,8 +8,8 @@
 //  cells  lane t holds row i0+t.  For every diagonal j of the band it computes
 //         the distance of cell (i0+t, i0+t+d_lo+j) and its rank
 //         r = #{k : eps_k < d} (one lookup in a bucket table of the
-//         thresholds, or a 5-step search over them) and stores r as byte
-//         [j][t] of a 32 x 32 rank matrix in shared memory.
+//         thresholds, or a 5-step search over them) and stores r as a byte of
+//         row j of a 32 x 32 rank matrix in shared memory.
 //  runs   lane j holds diagonal j.  It reads row j of the matrix (the ranks of
 //         its 32 cells, two 16-byte loads) and gathers their five bit planes:
 //         two words of four ranks are interleaved bit by bit, so one mask and
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(LTHREADS, 8) k_lines(CellArgs a, LineBufs lb, 
     uint32_t *pl = ws + O_PL, *pl4 = ws + O_PL4, *epsb = ws + O_EPS, *tab = ws + O_TAB;
     uint32_t *hs = ws + O_HS + lane;  // this lane's column: [l * 32], threshold kk (below)
     uint2 *lqa = reinterpret_cast<uint2 *>(ws + O_LQ);  // [k * LD + j]
-    unsigned char *rkm = reinterpret_cast<unsigned char *>(ws + O_LQ);  // rank matrix [j][t]
+    unsigned char *rkm = reinterpret_cast<unsigned char *>(ws + O_LQ);  // rank matrix, row j
     uint2 *lq = lqa + lane;                               // slots of this lane's diagonal
     const bool klane = lane < K;
     // byte of row `lane` in a row of the rank matrix: rows 8h + 2u and 8h + 2u + 1
